@@ -1,0 +1,293 @@
+"""CPU FP64 oracle for the ensemble-PCG / surrogate-grouping method of
+D'Elia, Phipps, Rushdi, Ebeida (arXiv 1705.02003).
+
+TEST INFRASTRUCTURE ONLY.  The product package never imports this module; only
+``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s cpu_baseline /
+reference arm do.  It shares no code with the CUDA path: the arithmetic lives
+in plain C (``problem.c``, ``pcg.c``, ``sgrid.c``, built with
+``-O2 -ffp-contract=off``), and this file only marshals numpy arrays.
+
+Parity status of each function is pinned by ``tests/test_oracle_*.py``
+(closed forms, manufactured solutions, brute force and the paper's printed
+conventions); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_SRC = ["problem.c", "pcg.c", "sgrid.c"]
+
+FD5_LOGKL = 1
+Q1_ROT = 2
+FD7_AXIS = 3
+
+CONVERGED, MAXIT, BREAKDOWN, BADINPUT = 0, 1, 2, 3
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C sources into ``oracle/_build/liboracle.so``."""
+    srcs = [os.path.join(_HERE, s) for s in _SRC]
+    hdr = os.path.join(_HERE, "oracle.h")
+    if not force and os.path.exists(_SO):
+        newest = max(os.path.getmtime(p) for p in srcs + [hdr])
+        if os.path.getmtime(_SO) >= newest:
+            return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp] + srcs + ["-lm", "-lpthread"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _declare(_lib)
+        return _lib
+
+
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+
+
+def _declare(L):
+    c = ctypes
+    L.or_problem_size.argtypes = [c.c_int, c.c_int, c.POINTER(c.c_int), c.POINTER(c.c_int64)]
+    L.or_pattern.argtypes = [c.c_int, c.c_int, _i64p, _i32p]
+    L.or_assemble.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, _f64p, _i64p, _i32p, _f64p, _f64p]
+    L.or_tensor.argtypes = [c.c_int, c.c_int, c.c_double, _f64p, _f64p, _f64p]
+    L.or_spmv.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, _f64p]
+    L.or_spmv.restype = None
+    L.or_jacobi.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p]
+    L.or_pcg.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_int, _f64p,
+                         c.POINTER(c.c_int), c.POINTER(c.c_double)]
+    L.or_solve_batch.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, c.c_int, _f64p, c.c_double,
+                                 c.c_int, c.c_int, _i32p, _i32p, _f64p, _f64p, c.c_void_p]
+    L.or_pcg_ir.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_double, c.c_int,
+                            c.c_int, _f64p, c.POINTER(c.c_int), c.POINTER(c.c_int),
+                            c.POINTER(c.c_double)]
+    L.or_adjoint_grad.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, _f64p, _f64p, c.c_double,
+                                  c.c_int, c.POINTER(c.c_double), _f64p, c.POINTER(c.c_int),
+                                  c.POINTER(c.c_int)]
+    L.or_sg_coord.argtypes = [c.c_int, c.c_int64]
+    L.or_sg_coord.restype = c.c_double
+    L.or_hat.argtypes = [c.c_int, c.c_int64, c.c_double]
+    L.or_hat.restype = c.c_double
+    L.or_sg_points.argtypes = [c.c_int, c.c_int, _i8p, _i32p, _f64p]
+    L.or_sg_points.restype = None
+    L.or_sg_eval.argtypes = [c.c_int, c.c_int, _i8p, _i32p, _f64p, c.c_int, _f64p, _f64p]
+    L.or_sg_eval.restype = None
+    L.or_sg_initial.argtypes = [c.c_int, c.c_int, c.c_int, _i8p, _i32p]
+    L.or_sg_refine.argtypes = [c.c_int, c.c_int, _i8p, _i32p, c.c_int, _f64p, c.c_double, c.c_int,
+                               c.c_int, _i8p, _i32p]
+    L.or_sort_perm.argtypes = [c.c_int, _f64p, _i32p]
+    L.or_sort_perm.restype = None
+    L.or_work_ratio.argtypes = [c.c_int, c.c_int, _i32p, _f64p]
+    L.or_work_ratio.restype = c.c_double
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# problem
+# ---------------------------------------------------------------------------
+def problem_size(kind: int, n: int):
+    J = ctypes.c_int()
+    nnz = ctypes.c_int64()
+    if lib().or_problem_size(kind, n, ctypes.byref(J), ctypes.byref(nnz)):
+        raise ValueError("bad problem kind/size")
+    return J.value, nnz.value
+
+
+def pattern(kind: int, n: int):
+    J, nnz = problem_size(kind, n)
+    rowptr = np.zeros(J + 1, np.int64)
+    colidx = np.zeros(nnz, np.int32)
+    if lib().or_pattern(kind, n, rowptr, colidx):
+        raise ValueError("pattern failed")
+    return rowptr, colidx
+
+
+def assemble(kind: int, n: int, nparam: int, aniso: float, xi, rowptr=None, colidx=None):
+    """One sample's CSR values (pattern order) and load vector."""
+    if rowptr is None:
+        rowptr, colidx = pattern(kind, n)
+    J = len(rowptr) - 1
+    vals = np.zeros(int(rowptr[-1]), np.float64)
+    b = np.zeros(J, np.float64)
+    rc = lib().or_assemble(kind, n, nparam, float(aniso), _f64(xi), rowptr, colidx, vals, b)
+    if rc:
+        raise ValueError(f"assemble failed ({rc})")
+    return vals, b
+
+
+def tensor(kind: int, nparam: int, aniso: float, xi, x):
+    d = 3 if kind == FD7_AXIS else 2
+    K = np.zeros(d * d, np.float64)
+    if lib().or_tensor(kind, nparam, float(aniso), _f64(xi), _f64(x), K):
+        raise ValueError("tensor failed")
+    return K.reshape(d, d)
+
+
+# ---------------------------------------------------------------------------
+# solver
+# ---------------------------------------------------------------------------
+def spmv(rowptr, colidx, vals, x):
+    J = len(rowptr) - 1
+    y = np.zeros(J, np.float64)
+    lib().or_spmv(J, rowptr, colidx, _f64(vals), _f64(x), y)
+    return y
+
+
+def jacobi(rowptr, colidx, vals):
+    J = len(rowptr) - 1
+    d = np.zeros(J, np.float64)
+    if lib().or_jacobi(J, rowptr, colidx, _f64(vals), d):
+        raise ValueError("missing diagonal")
+    return d
+
+
+def pcg(rowptr, colidx, vals, b, rtol: float, maxit: int):
+    """Per-sample Jacobi-PCG. Returns (x, iters, status, relres)."""
+    J = len(rowptr) - 1
+    x = np.zeros(J, np.float64)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().or_pcg(J, rowptr, colidx, _f64(vals), _f64(b), float(rtol), int(maxit), x,
+                      ctypes.byref(it), ctypes.byref(rr))
+    return x, it.value, st, rr.value
+
+
+def solve_batch(kind: int, n: int, nparam: int, aniso: float, xi, rtol: float, maxit: int,
+                nthreads: int = 1, want_x: bool = False):
+    """Assemble + solve each row of ``xi`` [M][N] independently.
+
+    Returns dict(iters, status, relres, G, x?) where G = ||u||_2^2."""
+    xi = _f64(xi)
+    M = xi.shape[0]
+    J, _ = problem_size(kind, n)
+    iters = np.zeros(M, np.int32)
+    status = np.zeros(M, np.int32)
+    relres = np.zeros(M, np.float64)
+    G = np.zeros(M, np.float64)
+    xout = np.zeros((M, J), np.float64) if want_x else None
+    ptr = xout.ctypes.data if want_x else None
+    rc = lib().or_solve_batch(kind, n, nparam, float(aniso), M, xi, float(rtol), int(maxit),
+                              int(nthreads), iters, status, relres, G, ptr)
+    if rc:
+        raise ValueError(f"solve_batch failed ({rc})")
+    out = dict(iters=iters, status=status, relres=relres, G=G)
+    if want_x:
+        out["x"] = xout
+    return out
+
+
+def pcg_ir(rowptr, colidx, vals, b, rtol_outer=1e-10, rtol_inner=1e-6, maxit_inner=20000,
+           maxit_outer=50):
+    J = len(rowptr) - 1
+    x = np.zeros(J, np.float64)
+    oi = ctypes.c_int()
+    ii = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().or_pcg_ir(J, rowptr, colidx, _f64(vals), _f64(b), float(rtol_outer),
+                         float(rtol_inner), int(maxit_inner), int(maxit_outer), x,
+                         ctypes.byref(oi), ctypes.byref(ii), ctypes.byref(rr))
+    return x, oi.value, ii.value, st, rr.value
+
+
+def adjoint_grad(kind: int, n: int, nparam: int, aniso: float, xi, w, rtol: float, maxit: int):
+    """Q = w^T u and dQ/dxi = -lambda^T (dA/dxi) u for one sample."""
+    grad = np.zeros(nparam, np.float64)
+    Q = ctypes.c_double()
+    itf = ctypes.c_int()
+    ita = ctypes.c_int()
+    st = lib().or_adjoint_grad(kind, n, nparam, float(aniso), _f64(xi), _f64(w), float(rtol),
+                               int(maxit), ctypes.byref(Q), grad, ctypes.byref(itf),
+                               ctypes.byref(ita))
+    if st < 0:
+        raise ValueError("adjoint_grad failed")
+    return Q.value, grad, itf.value, ita.value, st
+
+
+# ---------------------------------------------------------------------------
+# sparse grid + grouping
+# ---------------------------------------------------------------------------
+def sg_coord(l: int, i: int) -> float:
+    return lib().or_sg_coord(int(l), int(i))
+
+
+def hat(l: int, i: int, y: float) -> float:
+    return lib().or_hat(int(l), int(i), float(y))
+
+
+def sg_points(lvl, idx):
+    lvl = np.ascontiguousarray(lvl, np.int8)
+    idx = np.ascontiguousarray(idx, np.int32)
+    M, N = lvl.shape
+    y = np.zeros((M, N), np.float64)
+    lib().or_sg_points(N, M, lvl, idx, y)
+    return y
+
+
+def sg_eval(lvl, idx, surplus, yq):
+    lvl = np.ascontiguousarray(lvl, np.int8)
+    idx = np.ascontiguousarray(idx, np.int32)
+    yq = _f64(yq)
+    M, N = lvl.shape
+    Q = yq.shape[0]
+    out = np.zeros(Q, np.float64)
+    if Q:
+        lib().or_sg_eval(N, M, lvl, idx, _f64(surplus), Q, yq, out)
+    return out
+
+
+def sg_initial(N: int, level: int, max_out: int = 1 << 16):
+    lvl = np.zeros((max_out, N), np.int8)
+    idx = np.zeros((max_out, N), np.int32)
+    M = lib().or_sg_initial(N, level, max_out, lvl, idx)
+    if M < 0:
+        raise ValueError("sg_initial overflow")
+    return lvl[:M].copy(), idx[:M].copy()
+
+
+def sg_refine(lvl, idx, first: int, surplus, tau: float, max_level: int, max_out: int = 1 << 16):
+    lvl = np.ascontiguousarray(lvl, np.int8)
+    idx = np.ascontiguousarray(idx, np.int32)
+    M, N = lvl.shape
+    ol = np.zeros((max_out, N), np.int8)
+    oi = np.zeros((max_out, N), np.int32)
+    cnt = lib().or_sg_refine(N, M, lvl, idx, int(first), _f64(surplus), float(tau), int(max_level),
+                             max_out, ol, oi)
+    if cnt < 0:
+        raise ValueError("sg_refine overflow")
+    return ol[:cnt].copy(), oi[:cnt].copy()
+
+
+def sort_perm(keys):
+    keys = _f64(keys)
+    perm = np.zeros(len(keys), np.int32)
+    lib().or_sort_perm(len(keys), keys, perm)
+    return perm
+
+
+def work_ratio(S: int, perm, iters) -> float:
+    perm = np.ascontiguousarray(perm, np.int32)
+    return lib().or_work_ratio(int(S), len(perm), perm, _f64(iters))

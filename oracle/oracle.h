@@ -1,0 +1,96 @@
+/*
+ * oracle.h -- plain CPU FP64 restatement of the ensemble-grouping method of
+ * D'Elia, Phipps, Rushdi, Ebeida, "Surrogate-based Ensemble Grouping Strategies
+ * for Embedded Sampling-based UQ" (arXiv 1705.02003).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
+ * calls this code; only the tests, __graft_entry__.smoke() and the bench's
+ * cpu_baseline / reference arm use it.  It shares no header, helper, table or
+ * constant with the CUDA path.
+ *
+ * Everything here is deliberately slow and obvious: per-sample loops, plain
+ * left-to-right sums, no blocking, no fused multiply-add (built with
+ * -ffp-contract=off).
+ *
+ * Problem kinds (the spatial discretisation of Eq. (elliptic-SPDE),
+ * -div(A grad u) = f on the unit square/cube, u = 0 on the boundary):
+ *   OR_FD5_LOGKL   2-D 5-point finite differences, n x n interior nodes,
+ *                  A = exp(0.5 * sum_{k=1}^{N-1} xi_{k+1} phi_k / k) diag(1, 10^(aniso xi_1)),
+ *                  f = 1.  N = nparam in 2..8.
+ *   OR_Q1_ROT      2-D bilinear (Q1) finite elements, 9-point stencil,
+ *                  A = a R(theta) diag(1, 10^(aniso xi_1)) R(theta)^T,
+ *                  theta = pi/4 (1 + xi_3), log a = 0.5 (xi_2 phi_1 + xi_4 phi_2 / 2),
+ *                  f = 1.  N = 4.
+ *   OR_FD7_AXIS    3-D 7-point finite differences,
+ *                  A = diag(1, 10^(aniso xi_1), 10^(aniso xi_2)) exp(0.3 sum_{k=3}^{6} xi_k phi_k),
+ *                  f = 1.  N = 6.
+ * phi_k are products of sines sin(m pi x_d); the mode lists are in problem.c.
+ * The log-coefficient form follows Eq. (diff-coeff); the tensor forms are the
+ * anisotropic A(x, y) of Section 2.1 / Section 4.
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_FD5_LOGKL = 1, OR_Q1_ROT = 2, OR_FD7_AXIS = 3 };
+
+/* Per-sample PCG outcome codes. */
+enum { OR_CONVERGED = 0, OR_MAXIT = 1, OR_BREAKDOWN = 2, OR_BADINPUT = 3 };
+
+/* ---- problem.c ---------------------------------------------------------- */
+int  or_problem_size(int kind, int n, int *J, int64_t *nnz);
+int  or_pattern(int kind, int n, int64_t *rowptr, int32_t *colidx);
+/* One sample: matrix values in the pattern's order and the load vector. */
+int  or_assemble(int kind, int n, int nparam, double aniso, const double *xi,
+                 const int64_t *rowptr, const int32_t *colidx,
+                 double *vals, double *b);
+/* The diffusion tensor at one point (row-major d x d); used by the tests'
+ * manufactured-solution and eigenvalue checks through its effect only. */
+int  or_tensor(int kind, int nparam, double aniso, const double *xi,
+               const double *x, double *K);
+
+/* ---- pcg.c -------------------------------------------------------------- */
+void or_spmv(int J, const int64_t *rowptr, const int32_t *colidx,
+             const double *vals, const double *x, double *y);
+int  or_jacobi(int J, const int64_t *rowptr, const int32_t *colidx,
+               const double *vals, double *dinv);
+int  or_pcg(int J, const int64_t *rowptr, const int32_t *colidx,
+            const double *vals, const double *b, double rtol, int maxit,
+            double *x, int *iters, double *relres);
+/* Assemble + solve M samples, one sample per thread at a time. */
+int  or_solve_batch(int kind, int n, int nparam, double aniso, int M,
+                    const double *xi, double rtol, int maxit, int nthreads,
+                    int *iters, int *status, double *relres, double *G,
+                    double *xout /* [M][J] or NULL */);
+/* Mixed precision: FP32 inner Jacobi-PCG inside FP64 iterative refinement. */
+int  or_pcg_ir(int J, const int64_t *rowptr, const int32_t *colidx,
+               const double *vals, const double *b, double rtol_outer,
+               double rtol_inner, int maxit_inner, int maxit_outer,
+               double *x, int *outer_its, int *inner_its, double *relres);
+/* Adjoint gradient of Q = w^T u for the FD kinds. */
+int  or_adjoint_grad(int kind, int n, int nparam, double aniso, const double *xi,
+                     const double *w, double rtol, int maxit,
+                     double *Q, double *grad, int *iters_fwd, int *iters_adj);
+
+/* ---- sgrid.c ------------------------------------------------------------ */
+double or_sg_coord(int l, int64_t i);
+double or_hat(int l, int64_t i, double y);
+void   or_sg_points(int N, int M, const int8_t *lvl, const int32_t *idx, double *y);
+void   or_sg_eval(int N, int M, const int8_t *lvl, const int32_t *idx,
+                  const double *surplus, int Q, const double *yq, double *out);
+int    or_sg_initial(int N, int level, int max_out, int8_t *lvl, int32_t *idx);
+int    or_sg_refine(int N, int M, const int8_t *lvl, const int32_t *idx,
+                    int first, const double *surplus, double tau, int max_level,
+                    int max_out, int8_t *out_lvl, int32_t *out_idx);
+void   or_sort_perm(int M, const double *keys, int32_t *perm);
+double or_work_ratio(int S, int M, const int32_t *perm, const double *iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

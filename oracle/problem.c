@@ -1,0 +1,246 @@
+/*
+ * problem.c -- oracle: grid graph and per-sample assembly of the discrete
+ * systems L_m U_m = F_m of Eq. (discrete-sys) for the stochastic elliptic
+ * problem of Eq. (elliptic-SPDE).
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Grid: h = 1/(n+1); interior nodes at x = (i+1) h, i = 0..n-1 per axis;
+ * unknowns in lexicographic order with x fastest.  Dirichlet neighbours are
+ * zero and are dropped from the graph.
+ *
+ * FD (5-point 2-D, 7-point 3-D), flux form:
+ *     (A u)_p = sum over the 2d faces f of p:  k_f (u_p - u_nbr) / h^2,
+ * where k_f is the diagonal tensor entry for the face's axis evaluated at the
+ * face midpoint; a boundary face contributes only to the diagonal.
+ * Load b_p = f = 1.
+ *
+ * Q1 (2-D bilinear elements of side h, 9-point stencil): the tensor is
+ * evaluated once per element at its centroid and the exact element stiffness
+ * int grad(phi_a) . K grad(phi_b) of a constant tensor is assembled element
+ * by element in lexicographic element order.  Load b_p = int f phi_p = h^2.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+
+/* KL-style sine modes (m_x, m_y) used by the 2-D log-coefficient fields. */
+static const int MODES2[7][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 1}, {1, 3}, {3, 2}};
+/* Tensor-sine modes (m_x, m_y, m_z) for xi_3..xi_6 of the 3-D field. */
+static const int MODES3[4][3] = {{1, 1, 1}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}};
+
+static double sinmode(int m, double x) { return sin(M_PI * (double)m * x); }
+
+int or_problem_size(int kind, int n, int *J, int64_t *nnz)
+{
+    if (n < 1) return -1;
+    int64_t nn = n;
+    switch (kind) {
+    case OR_FD5_LOGKL: *J = (int)(nn * nn); *nnz = 5 * nn * nn - 4 * nn; return 0;
+    case OR_Q1_ROT:    *J = (int)(nn * nn); *nnz = (3 * nn - 2) * (3 * nn - 2); return 0;
+    case OR_FD7_AXIS:  *J = (int)(nn * nn * nn); *nnz = 7 * nn * nn * nn - 6 * nn * nn; return 0;
+    default: return -1;
+    }
+}
+
+/* Graph of one row: neighbours listed in increasing column order. */
+int or_pattern(int kind, int n, int64_t *rowptr, int32_t *colidx)
+{
+    int64_t k = 0;
+    rowptr[0] = 0;
+    if (kind == OR_FD5_LOGKL) {
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+                int p = i + n * j;
+                if (j > 0) colidx[k++] = p - n;
+                if (i > 0) colidx[k++] = p - 1;
+                colidx[k++] = p;
+                if (i < n - 1) colidx[k++] = p + 1;
+                if (j < n - 1) colidx[k++] = p + n;
+                rowptr[p + 1] = k;
+            }
+        return 0;
+    }
+    if (kind == OR_Q1_ROT) {
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < n; i++) {
+                int p = i + n * j;
+                for (int dj = -1; dj <= 1; dj++)
+                    for (int di = -1; di <= 1; di++) {
+                        int ii = i + di, jj = j + dj;
+                        if (ii < 0 || ii >= n || jj < 0 || jj >= n) continue;
+                        colidx[k++] = ii + n * jj;
+                    }
+                rowptr[p + 1] = k;
+            }
+        return 0;
+    }
+    if (kind == OR_FD7_AXIS) {
+        int n2 = n * n;
+        for (int l = 0; l < n; l++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    int p = i + n * j + n2 * l;
+                    if (l > 0) colidx[k++] = p - n2;
+                    if (j > 0) colidx[k++] = p - n;
+                    if (i > 0) colidx[k++] = p - 1;
+                    colidx[k++] = p;
+                    if (i < n - 1) colidx[k++] = p + 1;
+                    if (j < n - 1) colidx[k++] = p + n;
+                    if (l < n - 1) colidx[k++] = p + n2;
+                    rowptr[p + 1] = k;
+                }
+        return 0;
+    }
+    return -1;
+}
+
+/* The diffusion tensor A(x, xi) (row-major d x d). */
+int or_tensor(int kind, int nparam, double aniso, const double *xi, const double *x, double *K)
+{
+    if (kind == OR_FD5_LOGKL) {
+        /* log a = 0.5 * sum_{k=1}^{N-1} xi_{k+1} phi_k(x) / k    (Eq. diff-coeff, log form) */
+        if (nparam < 1 || nparam > 8) return -1;
+        double s = 0.0;
+        for (int k = 1; k < nparam; k++) {
+            double phi = sinmode(MODES2[k - 1][0], x[0]) * sinmode(MODES2[k - 1][1], x[1]);
+            s = s + (xi[k] * phi) / (double)k;
+        }
+        double a = exp(0.5 * s);
+        K[0] = a;
+        K[1] = 0.0;
+        K[2] = 0.0;
+        K[3] = a * pow(10.0, aniso * xi[0]);
+        return 0;
+    }
+    if (kind == OR_Q1_ROT) {
+        if (nparam != 4) return -1;
+        double phi1 = sinmode(1, x[0]) * sinmode(1, x[1]);
+        double phi2 = sinmode(2, x[0]) * sinmode(1, x[1]);
+        double a = exp(0.5 * (xi[1] * phi1 + (xi[3] * phi2) / 2.0));
+        double theta = (M_PI / 4.0) * (1.0 + xi[2]);
+        double c = cos(theta), s = sin(theta);
+        double d2 = pow(10.0, aniso * xi[0]);
+        /* R diag(1, d2) R^T with R = [[c, -s], [s, c]] */
+        K[0] = a * (c * c + s * s * d2);
+        K[1] = a * (c * s * (1.0 - d2));
+        K[2] = K[1];
+        K[3] = a * (s * s + c * c * d2);
+        return 0;
+    }
+    if (kind == OR_FD7_AXIS) {
+        if (nparam != 6) return -1;
+        double s = 0.0;
+        for (int k = 0; k < 4; k++) {
+            double phi = sinmode(MODES3[k][0], x[0]) * sinmode(MODES3[k][1], x[1]) *
+                         sinmode(MODES3[k][2], x[2]);
+            s = s + xi[2 + k] * phi;
+        }
+        double e = exp(0.3 * s);
+        for (int q = 0; q < 9; q++) K[q] = 0.0;
+        K[0] = e;
+        K[4] = e * pow(10.0, aniso * xi[0]);
+        K[8] = e * pow(10.0, aniso * xi[1]);
+        return 0;
+    }
+    return -1;
+}
+
+static int64_t find_col(const int64_t *rowptr, const int32_t *colidx, int row, int col)
+{
+    for (int64_t k = rowptr[row]; k < rowptr[row + 1]; k++)
+        if (colidx[k] == col) return k;
+    return -1;
+}
+
+/* Coordinate of a (half-)integer grid position t, i.e. t * h. */
+static double coord(double t, int n) { return t / (double)(n + 1); }
+
+static int assemble_fd(int kind, int n, int nparam, double aniso, const double *xi,
+                       const int64_t *rowptr, const int32_t *colidx, double *vals, double *b)
+{
+    int d = (kind == OR_FD7_AXIS) ? 3 : 2;
+    double ih2 = (double)(n + 1) * (double)(n + 1);
+    int J = (d == 3) ? n * n * n : n * n;
+    double K[9];
+    for (int p = 0; p < J; p++) {
+        int g[3] = {p % n, (p / n) % n, (d == 3) ? p / (n * n) : 0};
+        int stride[3] = {1, n, n * n};
+        /* faces in increasing column order: -z, -y, -x, +x, +y, +z */
+        double diag = 0.0;
+        for (int side = 0; side < 2; side++) {
+            for (int q = 0; q < d; q++) {
+                int axis = (side == 0) ? d - 1 - q : q;
+                int dir = (side == 0) ? -1 : 1;
+                double xm[3];
+                for (int a = 0; a < d; a++) xm[a] = coord((double)g[a] + 1.0, n);
+                xm[axis] = coord((double)g[axis] + 1.0 + 0.5 * dir, n);
+                if (or_tensor(kind, nparam, aniso, xi, xm, K)) return -1;
+                double kf = K[axis * d + axis];
+                diag = diag + kf;
+                int nb = g[axis] + dir;
+                if (nb >= 0 && nb < n) {
+                    int64_t pos = find_col(rowptr, colidx, p, p + dir * stride[axis]);
+                    if (pos < 0) return -2;
+                    vals[pos] = -(kf * ih2);
+                }
+            }
+        }
+        int64_t pd = find_col(rowptr, colidx, p, p);
+        if (pd < 0) return -2;
+        vals[pd] = diag * ih2;
+        b[p] = 1.0;
+    }
+    return 0;
+}
+
+static int assemble_q1(int n, int nparam, double aniso, const double *xi,
+                       const int64_t *rowptr, const int32_t *colidx, double *vals, double *b)
+{
+    int J = n * n;
+    for (int64_t k = 0; k < rowptr[J]; k++) vals[k] = 0.0;
+    /* Reference-square integrals of products of 1-D factors:
+       int (1-s)^2 = int s^2 = 1/3, int s(1-s) = 1/6, int d/ds(.) against a
+       1-D factor = 1/2; the sign of d/ds is -1 for (1-s) and +1 for s. */
+    double sg[2] = {-1.0, 1.0};
+    double Mm[2][2] = {{1.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 1.0 / 3.0}};
+    double K[4];
+    for (int ey = 0; ey <= n; ey++)
+        for (int ex = 0; ex <= n; ex++) {
+            double xc[2] = {coord((double)ex + 0.5, n), coord((double)ey + 0.5, n)};
+            if (or_tensor(OR_Q1_ROT, nparam, aniso, xi, xc, K)) return -1;
+            for (int l = 0; l < 4; l++) {
+                int al = l & 1, bl = l >> 1;
+                int nxl = ex + al, nyl = ey + bl; /* node coords 0..n+1 */
+                if (nxl < 1 || nxl > n || nyl < 1 || nyl > n) continue;
+                int row = (nxl - 1) + n * (nyl - 1);
+                for (int m = 0; m < 4; m++) {
+                    int am = m & 1, bm = m >> 1;
+                    int nxm = ex + am, nym = ey + bm;
+                    if (nxm < 1 || nxm > n || nym < 1 || nym > n) continue;
+                    int col = (nxm - 1) + n * (nym - 1);
+                    double c1 = sg[al] * sg[am] * Mm[bl][bm]; /* d/dx d/dx */
+                    double c2 = sg[bl] * sg[bm] * Mm[al][am]; /* d/dy d/dy */
+                    double c3 = (sg[al] * sg[bm] + sg[bl] * sg[am]) / 4.0; /* mixed */
+                    double ke = K[0] * c1 + K[3] * c2 + K[1] * c3;
+                    int64_t pos = find_col(rowptr, colidx, row, col);
+                    if (pos < 0) return -2;
+                    vals[pos] = vals[pos] + ke;
+                }
+            }
+        }
+    double bh = 1.0 / ((double)(n + 1) * (double)(n + 1));
+    for (int p = 0; p < J; p++) b[p] = bh;
+    return 0;
+}
+
+int or_assemble(int kind, int n, int nparam, double aniso, const double *xi,
+                const int64_t *rowptr, const int32_t *colidx, double *vals, double *b)
+{
+    if (kind == OR_FD5_LOGKL || kind == OR_FD7_AXIS)
+        return assemble_fd(kind, n, nparam, aniso, xi, rowptr, colidx, vals, b);
+    if (kind == OR_Q1_ROT)
+        return assemble_q1(n, nparam, aniso, xi, rowptr, colidx, vals, b);
+    return -1;
+}

@@ -1,0 +1,183 @@
+/*
+ * ens.h -- C ABI of libens: ensemble Jacobi-PCG for parametrised anisotropic
+ * diffusion on one GB300 (sm_103a), with surrogate-based ensemble grouping.
+ *
+ * Method: D'Elia, Phipps, Rushdi, Ebeida, "Surrogate-based Ensemble Grouping
+ * Strategies for Embedded Sampling-based Uncertainty Quantification"
+ * (arXiv 1705.02003).  Each entry point cites the passage that defines what it
+ * computes.
+ *
+ * Conventions for every call
+ *   - Pointers are DEVICE memory owned by the caller unless marked (host).
+ *     The library never frees or keeps caller memory beyond the call.
+ *   - `stream` is a cudaStream_t (passed as void*); work is queued on it and the
+ *     call returns without waiting unless the entry point says otherwise.
+ *   - Layout of ensemble data ("commuted Kronecker" order, Eq. discrete-comm-kron-sys):
+ *       matrix values  vals[E][nnz][S]   -- lane (sample) index fastest
+ *       vectors        v[E][J][S]
+ *       per-lane data  a[E][S]
+ *     E ensembles of S samples share one CSR graph (rowptr[J+1], colidx[nnz],
+ *     int32, rows sorted by column).  S must be 1, 2, 4, 8, 16, 32 or 64.
+ *   - Return value: ENS_OK (0) or a negative ENS_E* code; the handle keeps a
+ *     message (ens_last_error).  No entry point aborts, traps or spins without
+ *     a bound.  Per-sample outcomes are reported in status[] (ENS_LANE_*).
+ */
+#ifndef ENS_H
+#define ENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ENS_VERSION 1
+
+enum {
+    ENS_OK = 0,
+    ENS_EINVAL = -1,   /* bad argument: null pointer, size, S not supported, ... */
+    ENS_ECUDA = -2,    /* a CUDA runtime error; message in ens_last_error */
+    ENS_ENOMEM = -3,   /* caller workspace smaller than the *_workspace_size answer */
+    ENS_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    ENS_ENOTSUP = -5   /* combination not implemented (e.g. adjoint of the Q1 problem) */
+};
+
+/* Per-sample ("lane") outcome of a solve. */
+enum {
+    ENS_LANE_CONVERGED = 0, /* ||r||_2 <= rtol ||b||_2 reached */
+    ENS_LANE_MAXIT = 1,     /* maxit iterations without convergence */
+    ENS_LANE_BREAKDOWN = 2, /* p^T A p <= 0 or not finite: lane frozen, x kept */
+    ENS_LANE_BADINPUT = 3,  /* b^T b or r^T D^-1 r not finite at the start */
+    ENS_LANE_INACTIVE = 4   /* lane masked out by the caller (padding) */
+};
+
+/* Spatial problems: -div(A(x, xi) grad u) = f on the unit square/cube,
+ * u = 0 on the boundary (Eq. elliptic-SPDE), with the tensor A built from
+ * the log-form coefficient of Eq. (diff-coeff).  h = 1/(n+1); unknowns are
+ * the n^d interior nodes in lexicographic order, x fastest.
+ *   ENS_FD5_LOGKL  2-D 5-point FD, A = exp(0.5 sum_{k=1}^{N-1} xi_{k+1} phi_k / k)
+ *                  diag(1, 10^(aniso xi_1)), f = 1; 2 <= N <= 8.
+ *                  phi_k = sin(a pi x) sin(b pi y), (a,b) = (1,1), (2,1), (1,2),
+ *                  (2,2), (3,1), (1,3), (3,2).  Face coefficients at face midpoints.
+ *   ENS_Q1_ROT     2-D bilinear FEM (9-point), A = a R(t) diag(1, 10^(aniso xi_1)) R(t)^T,
+ *                  t = pi/4 (1 + xi_3), log a = 0.5 (xi_2 phi_1 + xi_4 phi_2 / 2), f = 1;
+ *                  N = 4.  Tensor at element centroids, exact element stiffness.
+ *   ENS_FD7_AXIS   3-D 7-point FD, A = diag(1, 10^(aniso xi_1), 10^(aniso xi_2))
+ *                  exp(0.3 sum_{k=3}^{6} xi_k phi_k), phi = sin(a pi x) sin(b pi y) sin(c pi z),
+ *                  (a,b,c) = (1,1,1), (2,1,1), (1,2,1), (1,1,2); f = 1; N = 6. */
+enum { ENS_FD5_LOGKL = 1, ENS_Q1_ROT = 2, ENS_FD7_AXIS = 3 };
+
+typedef struct {
+    int kind;     /* ENS_FD5_LOGKL | ENS_Q1_ROT | ENS_FD7_AXIS */
+    int n;        /* interior nodes per axis, >= 2 */
+    int nparam;   /* N, random parameters per sample */
+    double aniso; /* exponent scale of the axis anisotropy */
+} ens_problem;
+
+typedef struct ens_ctx *ens_handle;
+
+/* Create a handle bound to CUDA device `device` (it becomes current for the
+ * calling thread).  The handle owns a private capture stream and a cache of
+ * instantiated CUDA graphs (keyed by every pointer and size of a solve); it is
+ * not thread-safe.  ens_destroy releases both. */
+int ens_create(ens_handle *h, int device);
+int ens_destroy(ens_handle h);
+/* (host) message of the last failed call on this handle; never NULL. */
+const char *ens_last_error(ens_handle h);
+
+/* (host) J and nnz of the problem's graph.  No device work. */
+int ens_problem_size(const ens_problem *p, int *J, int64_t *nnz);
+
+/* The shared sparsity graph of Eqs. (discrete-sys)/(discrete-comm-kron-sys):
+ * writes rowptr[J+1] and colidx[nnz] (device, int32). */
+int ens_pattern(ens_handle h, const ens_problem *p, int32_t *rowptr, int32_t *colidx,
+                void *stream);
+
+/* Ensemble assembly (Section 2.3, "storing each nonzero entry as a length-S
+ * array"): for E ensembles of S samples with parameters xi[E][S][nparam]
+ * (device, f64), writes the sample-interleaved values vals[E][nnz][S]
+ * (f64, or f32 when vals_f32 != 0), the Jacobi inverse diagonal dinv[E][J][S]
+ * and the load b[E][J][S] (both f64; either may be NULL).  A NaN parameter
+ * gives NaN values in its lane only. */
+int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, const double *xi,
+                 const int32_t *rowptr, const int32_t *colidx, void *vals, int vals_f32,
+                 double *dinv, double *b, void *stream);
+
+/* Bytes of caller workspace ens_pcg_solve needs (device memory, 256-byte aligned). */
+size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E);
+
+/* Ensemble Jacobi-PCG with per-sample inner products and norms (Section 2.3:
+ * the ensemble inner product is taken per component so each sample converges
+ * at its own rate; Section 4: per-sample convergence record and the zero
+ * A-conjugate-norm guard).  Solves A_s x_s = b_s for every active lane s of
+ * every ensemble, from x = 0, to ||r_s||_2 <= rtol ||b_s||_2 on the
+ * recursively updated residual; a converged, broken-down or maxit lane is
+ * frozen (no further updates) while the others continue.
+ *   active[E][S]  (device u8, may be NULL = all active) 0 marks a padding lane.
+ *   x[E][J][S]    output (written for every lane; 0 for inactive lanes).
+ *   iters[E][S], relres[E][S], status[E][S]  outputs (relres = ||r||/||b||).
+ *   work          caller scratch of at least ens_pcg_workspace_size bytes.
+ * The iteration runs inside one CUDA graph with a device-evaluated while loop
+ * (at most maxit trips), so the call does not synchronise the stream. */
+int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
+                  const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                  const double *dinv, const double *b, double *x, const uint8_t *active,
+                  double rtol, int maxit, int32_t *iters, double *relres, int32_t *status,
+                  void *work, size_t work_bytes, void *stream);
+
+/* Surrogate-based grouping (Section 3.1, "SGS-based grouping", Eq. SGSiterations):
+ * evaluates the hierarchical piecewise-linear sparse-grid surrogate
+ *   pred[q] = sum_{m<M} surplus[m] prod_n psi_{lvl[m][n], idx[m][n]}(yq[q][n])
+ * (hat basis of Section 2.2, summed in m order) at Mq points yq[Mq][N], then
+ * returns perm[Mq], the stable ascending order of pred (ties keep index order),
+ * which cut into consecutive runs of S forms the ensembles; *n_ens (host) =
+ * ceil(Mq / S), the last ensemble padded.  M may be 0 (pred = 0, identity).
+ * lvl[M][N] int8, idx[M][N] int32, surplus[M] f64: device.  Mq <= 16384. */
+int ens_group(ens_handle h, int N, int M, const int8_t *lvl, const int32_t *idx,
+              const double *surplus, int Mq, const double *yq, int S, double *pred,
+              int32_t *perm, int *n_ens, void *stream);
+
+/* The surrogate alone (Eq. SGSiterations / SGSoutput), same arithmetic as
+ * ens_group: out[q] = sum_m surplus[m] psi_m(yq[q]).  When values[Mq]
+ * (device) is given, out[q] = values[q] - that sum instead: the hierarchical
+ * surplus of Eq. (hierSGint) of a new point, because every basis function of a
+ * point at the same or a finer level vanishes there (the triangularity noted
+ * beside the hierarchisation system). */
+int ens_sg_eval(ens_handle h, int N, int M, const int8_t *lvl, const int32_t *idx,
+                const double *surplus, int Mq, const double *yq, const double *values,
+                double *out, void *stream);
+
+/* Per-sample quantity of interest of a solution x[E][J][S] (device):
+ *   w == NULL:  out[e][s] = sum_j x[e][j][s]^2      (G = ||u||_l2^2, Section 4)
+ *   w != NULL:  out[e][s] = sum_j w[j] x[e][j][s]   (a weighted mean, e.g. G_u of
+ *                                                   Section 2.1 over a region)
+ * Each ensemble is summed by one block in a fixed order (deterministic). */
+int ens_qoi(ens_handle h, int J, int S, int E, const double *x, const double *w, double *out,
+            void *stream);
+
+/* The sort-and-chunk step of ens_group alone, on caller keys[Mq] (device):
+ * used for the natural (identity keys), random and iteration-sorted groupings. */
+int ens_sort_chunk(ens_handle h, int Mq, const double *keys, int S, int32_t *perm, int *n_ens,
+                   void *stream);
+
+/* (host) Classic adaptive refinement (Section 2.2, "Adaptivity"): every point
+ * m in [first, M) with |surplus[m]| >= tau gets its children -- per dimension
+ * n, (0,i) -> (1,1) and (l,i) -> (l+1, 2i-1), (l+1, 2i+1) for l >= 1 -- unless
+ * the child is already in the grid or already listed, or its level sum
+ * exceeds max_level.  Writes up to max_out children to out_lvl/out_idx (host,
+ * [.][N]) in generation order and returns their count, or a negative code.
+ * All arrays host memory. */
+int ens_sg_refine(int N, int M, const int8_t *lvl, const int32_t *idx, int first,
+                  const double *surplus, double tau, int max_level, int max_out,
+                  int8_t *out_lvl, int32_t *out_idx);
+
+/* (host) The full sparse grid of levels 0..level (Section 2.2, Z_l with
+ * alpha(l) = |l|): the 2^N corners (corner c has i_n = bit n of c), then
+ * `level` refinement rounds of every newest point.  Returns the count. */
+int ens_sg_initial(int N, int level, int max_out, int8_t *lvl, int32_t *idx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENS_H */

@@ -1,0 +1,365 @@
+// assemble.cu -- the shared graph and the ensemble assembly kernel (K1).
+//
+// Eq. (elliptic-SPDE) discretised on the unit square / cube (h = 1/(n+1),
+// interior nodes, x fastest).  The values of all S samples of an ensemble are
+// written interleaved, vals[e][k][s]: the commuted Kronecker layout of
+// Eq. (discrete-comm-kron-sys), one CSR graph for every sample.
+//
+//   FD (5/7-point, flux form):  (A u)_p = sum_f k_f (u_p - u_nbr) / h^2, with
+//       k_f the tensor's diagonal entry for the face axis at the face midpoint;
+//       boundary faces add to the diagonal only; f = 1.
+//   Q1 (9-point):  element stiffness int grad(phi_a) . K grad(phi_b) of the
+//       tensor evaluated at the element centroid, summed over the (up to) four
+//       elements shared by the two nodes in lexicographic element order; f = 1
+//       gives b = h^2.
+//
+// One thread per (ensemble, row, lane); lanes are fastest so every store of a
+// nonzero's S values is one contiguous run.
+#include "ens_common.cuh"
+
+namespace ens {
+
+namespace {
+
+__constant__ int kModes2[7][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 1}, {1, 3}, {3, 2}};
+__constant__ int kModes3[4][3] = {{1, 1, 1}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}};
+
+// ---- pattern ---------------------------------------------------------------
+// rowptr by a single-block scan of the per-row neighbour counts.
+__global__ void k_rowptr(int kind, int n, int J, int32_t *rowptr)
+{
+    __shared__ long long part[1024];
+    int t = threadIdx.x;
+    int chunk = (J + blockDim.x - 1) / blockDim.x;
+    int r0 = t * chunk, r1 = min(J, r0 + chunk);
+    int cols[9];
+    long long s = 0;
+    for (int r = r0; r < r1; r++) s += row_neighbours(kind, n, r, cols);
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        long long acc = 0;
+        for (int k = 0; k < (int)blockDim.x; k++) {
+            long long v = part[k];
+            part[k] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    long long acc = part[t];
+    if (t == 0) rowptr[0] = 0;
+    for (int r = r0; r < r1; r++) {
+        acc += row_neighbours(kind, n, r, cols);
+        rowptr[r + 1] = (int32_t)acc;
+    }
+}
+
+__global__ void k_colidx(int kind, int n, int J, const int32_t *__restrict__ rowptr,
+                         int32_t *__restrict__ colidx)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= J) return;
+    int cols[9];
+    int c = row_neighbours(kind, n, r, cols);
+    int32_t k0 = rowptr[r];
+    for (int q = 0; q < c; q++) colidx[k0 + q] = cols[q];
+}
+
+// ---- fields ------------------------------------------------------------------
+// log a for the 2-D FD field: 0.5 sum_{k=1}^{N-1} xi_k phi_k / k (xi 0-based).
+__device__ double fd5_a(const double *xi, int N, double x, double y)
+{
+    double s = 0.0;
+    for (int k = 1; k < N; k++) {
+        double phi = dmul(sinpi(kModes2[k - 1][0] * x), sinpi(kModes2[k - 1][1] * y));
+        s = dadd(s, dmul(xi[k], phi) / (double)k);
+    }
+    return exp(dmul(0.5, s));
+}
+
+__device__ double fd7_e(const double *xi, double x, double y, double z)
+{
+    double s = 0.0;
+    for (int k = 0; k < 4; k++) {
+        double phi = dmul(dmul(sinpi(kModes3[k][0] * x), sinpi(kModes3[k][1] * y)), sinpi(kModes3[k][2] * z));
+        s = dadd(s, dmul(xi[2 + k], phi));
+    }
+    return exp(dmul(0.3, s));
+}
+
+template <typename V>
+__device__ __forceinline__ void put(V *vals, long long idx, double v) { vals[idx] = (V)v; }
+
+// ---- FD 5-point ------------------------------------------------------------
+template <typename V>
+__global__ void k_assemble_fd5(int n, int N, double aniso, int S, int E, const double *__restrict__ xi,
+                               const int32_t *__restrict__ rowptr, V *__restrict__ vals,
+                               double *__restrict__ dinv, double *__restrict__ b, long long nnz)
+{
+    const int J = n * n;
+    const long long total = (long long)E * J * S;
+    const double den = (double)(n + 1);
+    const double ih2 = den * den;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int s = (int)(t % S);
+        long long er = t / S;
+        int row = (int)(er % J);
+        int e = (int)(er / J);
+        double x[8];
+        const double *xs = xi + ((long long)e * S + s) * N;
+        for (int k = 0; k < N; k++) x[k] = xs[k];
+        int i = row % n, j = row / n;
+        double d2 = exp10(dmul(aniso, x[0]));
+        double xc = (double)(i + 1) / den, yc = (double)(j + 1) / den;
+        double kS = dmul(fd5_a(x, N, xc, ((double)j + 0.5) / den), d2);
+        double kW = fd5_a(x, N, ((double)i + 0.5) / den, yc);
+        double kE = fd5_a(x, N, ((double)i + 1.5) / den, yc);
+        double kN = dmul(fd5_a(x, N, xc, ((double)j + 1.5) / den), d2);
+        double diag = dadd(dadd(dadd(kS, kW), kE), kN);
+        long long base = (long long)e * nnz * S + s;
+        long long k = rowptr[row];
+        if (j > 0) put(vals, base + (k++) * S, -dmul(kS, ih2));
+        if (i > 0) put(vals, base + (k++) * S, -dmul(kW, ih2));
+        double dv = dmul(diag, ih2);
+        put(vals, base + (k++) * S, dv);
+        if (i < n - 1) put(vals, base + (k++) * S, -dmul(kE, ih2));
+        if (j < n - 1) put(vals, base + (k++) * S, -dmul(kN, ih2));
+        long long vi = ((long long)e * J + row) * S + s;
+        if (dinv) dinv[vi] = 1.0 / dv;
+        if (b) b[vi] = 1.0;
+    }
+}
+
+// ---- FD 7-point ------------------------------------------------------------
+template <typename V>
+__global__ void k_assemble_fd7(int n, double aniso, int S, int E, const double *__restrict__ xi,
+                               const int32_t *__restrict__ rowptr, V *__restrict__ vals,
+                               double *__restrict__ dinv, double *__restrict__ b, long long nnz)
+{
+    const int n2 = n * n;
+    const int J = n2 * n;
+    const long long total = (long long)E * J * S;
+    const double den = (double)(n + 1);
+    const double ih2 = den * den;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int s = (int)(t % S);
+        long long er = t / S;
+        int row = (int)(er % J);
+        int e = (int)(er / J);
+        double x[6];
+        const double *xs = xi + ((long long)e * S + s) * 6;
+        for (int k = 0; k < 6; k++) x[k] = xs[k];
+        int i = row % n, j = (row / n) % n, l = row / n2;
+        double d2 = exp10(dmul(aniso, x[0]));
+        double d3 = exp10(dmul(aniso, x[1]));
+        double xc = (double)(i + 1) / den, yc = (double)(j + 1) / den, zc = (double)(l + 1) / den;
+        double kB = dmul(fd7_e(x, xc, yc, ((double)l + 0.5) / den), d3);
+        double kS = dmul(fd7_e(x, xc, ((double)j + 0.5) / den, zc), d2);
+        double kW = fd7_e(x, ((double)i + 0.5) / den, yc, zc);
+        double kE = fd7_e(x, ((double)i + 1.5) / den, yc, zc);
+        double kN = dmul(fd7_e(x, xc, ((double)j + 1.5) / den, zc), d2);
+        double kT = dmul(fd7_e(x, xc, yc, ((double)l + 1.5) / den), d3);
+        double diag = dadd(dadd(dadd(dadd(dadd(kB, kS), kW), kE), kN), kT);
+        long long base = (long long)e * nnz * S + s;
+        long long k = rowptr[row];
+        if (l > 0) put(vals, base + (k++) * S, -dmul(kB, ih2));
+        if (j > 0) put(vals, base + (k++) * S, -dmul(kS, ih2));
+        if (i > 0) put(vals, base + (k++) * S, -dmul(kW, ih2));
+        double dv = dmul(diag, ih2);
+        put(vals, base + (k++) * S, dv);
+        if (i < n - 1) put(vals, base + (k++) * S, -dmul(kE, ih2));
+        if (j < n - 1) put(vals, base + (k++) * S, -dmul(kN, ih2));
+        if (l < n - 1) put(vals, base + (k++) * S, -dmul(kT, ih2));
+        long long vi = ((long long)e * J + row) * S + s;
+        if (dinv) dinv[vi] = 1.0 / dv;
+        if (b) b[vi] = 1.0;
+    }
+}
+
+// ---- Q1 9-point --------------------------------------------------------------
+// Integrals on the reference square of products of the bilinear factors:
+// mass-like 1/3 (same end) or 1/6 (opposite ends); derivative signs -1 / +1.
+__device__ __forceinline__ double q1_mass(int u, int v) { return u == v ? 1.0 / 3.0 : 1.0 / 6.0; }
+__device__ __forceinline__ double q1_sign(int u) { return u ? 1.0 : -1.0; }
+
+template <typename V>
+__global__ void k_assemble_q1(int n, double aniso, int S, int E, const double *__restrict__ xi,
+                              const int32_t *__restrict__ rowptr, V *__restrict__ vals,
+                              double *__restrict__ dinv, double *__restrict__ b, long long nnz)
+{
+    const int J = n * n;
+    const long long total = (long long)E * J * S;
+    const double den = (double)(n + 1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int s = (int)(t % S);
+        long long er = t / S;
+        int row = (int)(er % J);
+        int e = (int)(er / J);
+        const double *xs = xi + ((long long)e * S + s) * 4;
+        double x0 = xs[0], x1 = xs[1], x2 = xs[2], x3 = xs[3];
+        int i = row % n, j = row / n;
+        // rotation and axis ratio are per sample; the log-coefficient per element
+        double th = dmul(0.25, dadd(1.0, x2));  // theta / pi
+        double c = cospi(th), sn = sinpi(th);
+        double d2 = exp10(dmul(aniso, x0));
+        double t11 = dadd(dmul(c, c), dmul(dmul(sn, sn), d2));
+        double t12 = dmul(dmul(c, sn), dsub(1.0, d2));
+        double t22 = dadd(dmul(sn, sn), dmul(dmul(c, c), d2));
+        // the four elements around node (i+1, j+1) in lexicographic order
+        double K0[4], K1[4], K3[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int ex = i + (q & 1), ey = j + (q >> 1);
+            double xc = ((double)ex + 0.5) / den, yc = ((double)ey + 0.5) / den;
+            double sy = sinpi(yc);
+            double phi1 = dmul(sinpi(xc), sy);
+            double phi2 = dmul(sinpi(2.0 * xc), sy);
+            double a = exp(dmul(0.5, dadd(dmul(x1, phi1), dmul(x3, phi2) / 2.0)));
+            K0[q] = dmul(a, t11);
+            K1[q] = dmul(a, t12);
+            K3[q] = dmul(a, t22);
+        }
+        long long base = (long long)e * nnz * S + s;
+        long long k = rowptr[row];
+        double dv = 1.0;
+        for (int dj = -1; dj <= 1; dj++)
+            for (int di = -1; di <= 1; di++) {
+                int ii = i + di, jj = j + dj;
+                if (ii < 0 || ii >= n || jj < 0 || jj >= n) continue;
+                double v = 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    int ex = i + (q & 1), ey = j + (q >> 1);
+                    // local coordinates of the row node and the column node
+                    int aR = (i + 1) - ex, bR = (j + 1) - ey;
+                    int aC = (ii + 1) - ex, bC = (jj + 1) - ey;
+                    if (aC < 0 || aC > 1 || bC < 0 || bC > 1) continue;
+                    double c1 = q1_sign(aR) * q1_sign(aC) * q1_mass(bR, bC);
+                    double c2 = q1_sign(bR) * q1_sign(bC) * q1_mass(aR, aC);
+                    double c3 = (q1_sign(aR) * q1_sign(bC) + q1_sign(bR) * q1_sign(aC)) / 4.0;
+                    double ke = dadd(dadd(dmul(K0[q], c1), dmul(K3[q], c2)), dmul(K1[q], c3));
+                    v = dadd(v, ke);
+                }
+                if (di == 0 && dj == 0) dv = v;
+                put(vals, base + (k++) * S, v);
+            }
+        long long vi = ((long long)e * J + row) * S + s;
+        if (dinv) dinv[vi] = 1.0 / dv;
+        if (b) b[vi] = 1.0 / (den * den);
+    }
+}
+
+unsigned grid_for(long long total, int block)
+{
+    long long g = (total + block - 1) / block;
+    const long long cap = 152LL * 64;  // a grid-stride loop beyond ~64 blocks per SM
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+int problem_check(const ens_problem *p, int *J, int64_t *nnz, std::string *why)
+{
+    if (!p) { *why = "null problem"; return ENS_EINVAL; }
+    long long n = p->n;
+    if (n < 2) { *why = "n must be >= 2"; return ENS_EINVAL; }
+    switch (p->kind) {
+    case ENS_FD5_LOGKL:
+        if (p->nparam < 2 || p->nparam > 8) { *why = "FD5 problem needs 2 <= nparam <= 8"; return ENS_EINVAL; }
+        if (n > 40000) { *why = "n too large"; return ENS_EINVAL; }
+        *J = (int)(n * n);
+        *nnz = 5 * n * n - 4 * n;
+        break;
+    case ENS_Q1_ROT:
+        if (p->nparam != 4) { *why = "Q1 problem needs nparam == 4"; return ENS_EINVAL; }
+        if (n > 20000) { *why = "n too large"; return ENS_EINVAL; }
+        *J = (int)(n * n);
+        *nnz = (3 * n - 2) * (3 * n - 2);
+        break;
+    case ENS_FD7_AXIS:
+        if (p->nparam != 6) { *why = "FD7 problem needs nparam == 6"; return ENS_EINVAL; }
+        if (n > 1000) { *why = "n too large"; return ENS_EINVAL; }
+        *J = (int)(n * n * n);
+        *nnz = 7 * n * n * n - 6 * n * n;
+        break;
+    default:
+        *why = "unknown problem kind";
+        return ENS_EINVAL;
+    }
+    if (*nnz >= (1LL << 31)) { *why = "nnz does not fit int32 column indices"; return ENS_EINVAL; }
+    return ENS_OK;
+}
+
+}  // namespace ens
+
+using namespace ens;
+
+extern "C" int ens_problem_size(const ens_problem *p, int *J, int64_t *nnz)
+{
+    std::string why;
+    if (!J || !nnz) return ENS_EINVAL;
+    return problem_check(p, J, nnz, &why);
+}
+
+extern "C" int ens_pattern(ens_handle h, const ens_problem *p, int32_t *rowptr, int32_t *colidx,
+                           void *stream)
+{
+    if (!h) return ENS_EINVAL;
+    int J;
+    int64_t nnz;
+    std::string why;
+    int rc = problem_check(p, &J, &nnz, &why);
+    if (rc) return set_error(h, rc, "ens_pattern: " + why);
+    if (!rowptr || !colidx) return set_error(h, ENS_EINVAL, "ens_pattern: null output");
+    cudaStream_t st = (cudaStream_t)stream;
+    k_rowptr<<<1, 1024, 0, st>>>(p->kind, p->n, J, rowptr);
+    ENS_LAUNCH_CHECK(h, "ens_pattern: rowptr kernel");
+    k_colidx<<<(J + 255) / 256, 256, 0, st>>>(p->kind, p->n, J, rowptr, colidx);
+    ENS_LAUNCH_CHECK(h, "ens_pattern: colidx kernel");
+    return ENS_OK;
+}
+
+extern "C" int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, const double *xi,
+                            const int32_t *rowptr, const int32_t *colidx, void *vals, int vals_f32,
+                            double *dinv, double *b, void *stream)
+{
+    if (!h) return ENS_EINVAL;
+    int J;
+    int64_t nnz;
+    std::string why;
+    int rc = problem_check(p, &J, &nnz, &why);
+    if (rc) return set_error(h, rc, "ens_assemble: " + why);
+    if (!lane_count_ok(S)) return set_error(h, ENS_EINVAL, "ens_assemble: S must be a power of two <= 64");
+    if (E < 0) return set_error(h, ENS_EINVAL, "ens_assemble: E < 0");
+    if (E == 0) return ENS_OK;
+    if (!xi || !rowptr || !colidx || !vals) return set_error(h, ENS_EINVAL, "ens_assemble: null pointer");
+    (void)colidx;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long total = (long long)E * J * S;
+    unsigned grid = grid_for(total, 256);
+    switch (p->kind) {
+    case ENS_FD5_LOGKL:
+        if (vals_f32)
+            k_assemble_fd5<float><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz);
+        else
+            k_assemble_fd5<double><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz);
+        break;
+    case ENS_Q1_ROT:
+        if (vals_f32)
+            k_assemble_q1<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz);
+        else
+            k_assemble_q1<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz);
+        break;
+    default:
+        if (vals_f32)
+            k_assemble_fd7<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz);
+        else
+            k_assemble_fd7<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz);
+        break;
+    }
+    ENS_LAUNCH_CHECK(h, "ens_assemble: kernel launch");
+    return ENS_OK;
+}

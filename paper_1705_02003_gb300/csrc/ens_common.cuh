@@ -1,0 +1,108 @@
+// ens_common.cuh -- internal declarations shared by the libens translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "ens.h"
+
+namespace ens {
+
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+
+}  // namespace ens
+
+struct ens_ctx {
+    int device = 0;
+    std::string last_error;
+    cudaStream_t capture = nullptr;          // private stream used only to capture graphs
+    std::vector<ens::GraphEntry> graphs;     // small LRU cache of instantiated loops
+    uint64_t clock = 0;
+};
+
+namespace ens {
+
+constexpr int kBlock = 256;  // threads per block of every vector/SpMV kernel
+
+inline int set_error(ens_ctx *h, int code, const std::string &msg)
+{
+    if (h) h->last_error = msg;
+    return code;
+}
+
+inline int cuda_error(ens_ctx *h, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return set_error(h, ENS_ECUDA, m);
+}
+
+#define ENS_CUDA_CHECK(h, expr)                                             \
+    do {                                                                    \
+        cudaError_t e_ = (expr);                                            \
+        if (e_ != cudaSuccess) return ens::cuda_error((h), e_, #expr);      \
+    } while (0)
+
+#define ENS_LAUNCH_CHECK(h, what)                                           \
+    do {                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                \
+        if (e_ != cudaSuccess) return ens::cuda_error((h), e_, what);       \
+    } while (0)
+
+inline bool lane_count_ok(int S)
+{
+    return S == 1 || S == 2 || S == 4 || S == 8 || S == 16 || S == 32 || S == 64;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Rounding-explicit FP64 helpers: each product and sum is rounded on its own
+// (no fused multiply-add), so a sum of products follows the same operation
+// sequence as a plain left-to-right host loop.
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// Neighbours of `row` in increasing column order; returns the count (<= 9).
+__device__ __host__ inline int row_neighbours(int kind, int n, int row, int *cols)
+{
+    int c = 0;
+    if (kind == ENS_FD5_LOGKL) {
+        int i = row % n, j = row / n;
+        if (j > 0) cols[c++] = row - n;
+        if (i > 0) cols[c++] = row - 1;
+        cols[c++] = row;
+        if (i < n - 1) cols[c++] = row + 1;
+        if (j < n - 1) cols[c++] = row + n;
+    } else if (kind == ENS_Q1_ROT) {
+        int i = row % n, j = row / n;
+        for (int dj = -1; dj <= 1; dj++)
+            for (int di = -1; di <= 1; di++) {
+                int ii = i + di, jj = j + dj;
+                if (ii >= 0 && ii < n && jj >= 0 && jj < n) cols[c++] = ii + n * jj;
+            }
+    } else {
+        int n2 = n * n;
+        int i = row % n, j = (row / n) % n, l = row / n2;
+        if (l > 0) cols[c++] = row - n2;
+        if (j > 0) cols[c++] = row - n;
+        if (i > 0) cols[c++] = row - 1;
+        cols[c++] = row;
+        if (i < n - 1) cols[c++] = row + 1;
+        if (j < n - 1) cols[c++] = row + n;
+        if (l < n - 1) cols[c++] = row + n2;
+    }
+    return c;
+}
+
+int problem_check(const ens_problem *p, int *J, int64_t *nnz, std::string *why);
+
+}  // namespace ens

@@ -1,0 +1,290 @@
+"""ctypes binding of libens (include/ens.h): the same entry points, taking torch
+tensors for device arrays and numpy arrays for host arrays.
+
+Argument marshalling only -- every step runs in the CUDA kernels of the
+library.  There is no CPU fallback: if the library cannot be built or loaded,
+``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FD5_LOGKL, Q1_ROT, FD7_AXIS = 1, 2, 3
+KINDS = {"fd5": FD5_LOGKL, "q1": Q1_ROT, "fd7": FD7_AXIS}
+
+OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5
+LANE_CONVERGED, LANE_MAXIT, LANE_BREAKDOWN, LANE_BADINPUT, LANE_INACTIVE = 0, 1, 2, 3, 4
+
+EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "ens_pattern",
+           "ens_assemble", "ens_pcg_workspace_size", "ens_pcg_solve", "ens_group", "ens_sort_chunk",
+           "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class EnsError(RuntimeError):
+    pass
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("nparam", ctypes.c_int),
+                ("aniso", ctypes.c_double)]
+
+
+def problem(kind, n: int, nparam: int, aniso: float) -> Problem:
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    return Problem(k, int(n), int(nparam), float(aniso))
+
+
+def load(path: str | None = None):
+    """Build (if stale) and load libens.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = path or _build.build()
+            L = ctypes.CDLL(so)
+            _declare(L)
+            _lib = L
+        return _lib
+
+
+def _declare(L):
+    c = ctypes
+    vp = c.c_void_p
+    L.ens_create.argtypes = [c.POINTER(vp), c.c_int]
+    L.ens_destroy.argtypes = [vp]
+    L.ens_last_error.argtypes = [vp]
+    L.ens_last_error.restype = c.c_char_p
+    L.ens_problem_size.argtypes = [c.POINTER(Problem), c.POINTER(c.c_int), c.POINTER(c.c_int64)]
+    L.ens_pattern.argtypes = [vp, c.POINTER(Problem), vp, vp, vp]
+    L.ens_assemble.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, c.c_int, vp,
+                               vp, vp]
+    L.ens_pcg_workspace_size.argtypes = [c.c_int, c.c_int64, c.c_int, c.c_int]
+    L.ens_pcg_workspace_size.restype = c.c_size_t
+    L.ens_pcg_solve.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp,
+                                c.c_double, c.c_int, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_group.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_int, vp, c.c_int, vp, vp,
+                            c.POINTER(c.c_int), vp]
+    L.ens_sort_chunk.argtypes = [vp, c.c_int, vp, c.c_int, vp, c.POINTER(c.c_int), vp]
+    L.ens_sg_eval.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_int, vp, vp, vp, vp]
+    L.ens_qoi.argtypes = [vp, c.c_int, c.c_int, c.c_int, vp, vp, vp, vp]
+    i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+    L.ens_sg_refine.argtypes = [c.c_int, c.c_int, i8p, i32p, c.c_int, f64p, c.c_double, c.c_int,
+                                c.c_int, i8p, i32p]
+    L.ens_sg_initial.argtypes = [c.c_int, c.c_int, c.c_int, i8p, i32p]
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("device array expected (CUDA tensor)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_dtype(t, dt, name):
+    if t is not None and t.dtype != dt:
+        raise TypeError(f"{name} must be {dt}, got {t.dtype}")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Handle:
+    """Owns an ens_handle (graph cache, capture stream) for one device."""
+
+    def __init__(self, device: int | None = None):
+        L = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        rc = L.ens_create(ctypes.byref(h), self.device)
+        if rc != OK:
+            raise EnsError(f"ens_create failed ({rc})")
+        self._h = h
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def check(self, rc, what):
+        if rc != OK:
+            msg = load().ens_last_error(self._h).decode()
+            raise EnsError(f"{what} failed ({rc}): {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ens_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def ens_problem_size(prob: Problem):
+    J = ctypes.c_int()
+    nnz = ctypes.c_int64()
+    rc = load().ens_problem_size(ctypes.byref(prob), ctypes.byref(J), ctypes.byref(nnz))
+    if rc != OK:
+        raise EnsError(f"ens_problem_size failed ({rc})")
+    return J.value, nnz.value
+
+
+def ens_pattern(h: Handle, prob: Problem, rowptr, colidx, stream=None):
+    _check_dtype(rowptr, torch.int32, "rowptr")
+    _check_dtype(colidx, torch.int32, "colidx")
+    J, nnz = ens_problem_size(prob)
+    if rowptr.numel() != J + 1 or colidx.numel() != nnz:
+        raise ValueError("rowptr/colidx sizes do not match the problem")
+    h.check(load().ens_pattern(h.ptr, ctypes.byref(prob), _ptr(rowptr), _ptr(colidx), _stream(stream)),
+            "ens_pattern")
+
+
+def ens_assemble(h: Handle, prob: Problem, S: int, E: int, xi, rowptr, colidx, vals, dinv=None, b=None,
+                 stream=None):
+    J, nnz = ens_problem_size(prob)
+    _check_dtype(xi, torch.float64, "xi")
+    if vals.dtype not in (torch.float64, torch.float32):
+        raise TypeError("vals must be float64 or float32")
+    if xi.numel() != E * S * prob.nparam or vals.numel() != E * nnz * S:
+        raise ValueError("xi / vals sizes do not match E, S, nparam, nnz")
+    for t, nm in ((dinv, "dinv"), (b, "b")):
+        if t is not None:
+            _check_dtype(t, torch.float64, nm)
+            if t.numel() != E * J * S:
+                raise ValueError(f"{nm} size does not match E * J * S")
+    rc = load().ens_assemble(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(xi), _ptr(rowptr),
+                             _ptr(colidx), _ptr(vals), int(vals.dtype == torch.float32), _ptr(dinv),
+                             _ptr(b), _stream(stream))
+    h.check(rc, "ens_assemble")
+
+
+def ens_pcg_workspace_size(J: int, nnz: int, S: int, E: int) -> int:
+    return int(load().ens_pcg_workspace_size(int(J), int(nnz), int(S), int(E)))
+
+
+def ens_pcg_solve(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx, vals, dinv, b, x, active,
+                  rtol: float, maxit: int, iters, relres, status, work, stream=None):
+    for t, nm, dt in ((vals, "vals", torch.float64), (dinv, "dinv", torch.float64), (b, "b", torch.float64),
+                      (x, "x", torch.float64), (iters, "iters", torch.int32), (relres, "relres", torch.float64),
+                      (status, "status", torch.int32), (rowptr, "rowptr", torch.int32),
+                      (colidx, "colidx", torch.int32)):
+        _check_dtype(t, dt, nm)
+    if active is not None:
+        _check_dtype(active, torch.uint8, "active")
+    if vals.numel() != E * nnz * S or x.numel() != E * J * S or iters.numel() != E * S:
+        raise ValueError("array sizes do not match E, J, nnz, S")
+    if work.dtype != torch.uint8:
+        raise TypeError("work must be a uint8 tensor")
+    rc = load().ens_pcg_solve(h.ptr, int(J), int(nnz), int(S), int(E), _ptr(rowptr), _ptr(colidx),
+                              _ptr(vals), _ptr(dinv), _ptr(b), _ptr(x), _ptr(active), float(rtol),
+                              int(maxit), _ptr(iters), _ptr(relres), _ptr(status), _ptr(work),
+                              work.numel(), _stream(stream))
+    h.check(rc, "ens_pcg_solve")
+
+
+def ens_group(h: Handle, lvl, idx, surplus, yq, S: int, pred, perm, stream=None) -> int:
+    M, N = (0, yq.shape[1]) if lvl is None else tuple(lvl.shape)
+    Mq = yq.shape[0]
+    _check_dtype(yq, torch.float64, "yq")
+    _check_dtype(pred, torch.float64, "pred")
+    _check_dtype(perm, torch.int32, "perm")
+    if M:
+        _check_dtype(lvl, torch.int8, "lvl")
+        _check_dtype(idx, torch.int32, "idx")
+        _check_dtype(surplus, torch.float64, "surplus")
+    n_ens = ctypes.c_int()
+    rc = load().ens_group(h.ptr, int(N), int(M), _ptr(lvl) if M else None, _ptr(idx) if M else None,
+                          _ptr(surplus) if M else None, int(Mq), _ptr(yq), int(S), _ptr(pred), _ptr(perm),
+                          ctypes.byref(n_ens), _stream(stream))
+    h.check(rc, "ens_group")
+    return n_ens.value
+
+
+def ens_sg_eval(h: Handle, lvl, idx, surplus, yq, out, values=None, stream=None):
+    """out = surrogate(yq), or values - surrogate(yq) (the surpluses) if values is given."""
+    M, N = (0, yq.shape[1]) if lvl is None else tuple(lvl.shape)
+    _check_dtype(yq, torch.float64, "yq")
+    _check_dtype(out, torch.float64, "out")
+    if values is not None:
+        _check_dtype(values, torch.float64, "values")
+    if M:
+        _check_dtype(lvl, torch.int8, "lvl")
+        _check_dtype(idx, torch.int32, "idx")
+        _check_dtype(surplus, torch.float64, "surplus")
+    rc = load().ens_sg_eval(h.ptr, int(N), int(M), _ptr(lvl) if M else None, _ptr(idx) if M else None,
+                            _ptr(surplus) if M else None, int(yq.shape[0]), _ptr(yq), _ptr(values),
+                            _ptr(out), _stream(stream))
+    h.check(rc, "ens_sg_eval")
+
+
+def ens_qoi(h: Handle, J: int, S: int, E: int, x, out, w=None, stream=None):
+    """out[e][s] = sum_j x^2 (w None) or sum_j w_j x (w a [J] tensor)."""
+    _check_dtype(x, torch.float64, "x")
+    _check_dtype(out, torch.float64, "out")
+    if w is not None:
+        _check_dtype(w, torch.float64, "w")
+        if w.numel() != J:
+            raise ValueError("w must have J entries")
+    if x.numel() != E * J * S or out.numel() != E * S:
+        raise ValueError("x / out sizes do not match E, J, S")
+    rc = load().ens_qoi(h.ptr, int(J), int(S), int(E), _ptr(x), _ptr(w), _ptr(out), _stream(stream))
+    h.check(rc, "ens_qoi")
+
+
+def ens_sort_chunk(h: Handle, keys, S: int, perm, stream=None) -> int:
+    _check_dtype(keys, torch.float64, "keys")
+    _check_dtype(perm, torch.int32, "perm")
+    n_ens = ctypes.c_int()
+    rc = load().ens_sort_chunk(h.ptr, int(keys.numel()), _ptr(keys), int(S), _ptr(perm),
+                               ctypes.byref(n_ens), _stream(stream))
+    h.check(rc, "ens_sort_chunk")
+    return n_ens.value
+
+
+def ens_sg_refine(lvl, idx, first: int, surplus, tau: float, max_level: int, max_out: int = 1 << 16):
+    """(host) children of the points first..M-1 with |surplus| >= tau."""
+    lvl = np.ascontiguousarray(lvl, np.int8)
+    idx = np.ascontiguousarray(idx, np.int32)
+    M, N = lvl.shape
+    ol = np.zeros((max_out, N), np.int8)
+    oi = np.zeros((max_out, N), np.int32)
+    cnt = load().ens_sg_refine(int(N), int(M), lvl, idx, int(first),
+                               np.ascontiguousarray(surplus, np.float64), float(tau), int(max_level),
+                               int(max_out), ol, oi)
+    if cnt < 0:
+        raise EnsError(f"ens_sg_refine failed ({cnt})")
+    return ol[:cnt].copy(), oi[:cnt].copy()
+
+
+def ens_sg_initial(N: int, level: int, max_out: int = 1 << 16):
+    """(host) the full sparse grid of levels 0..level."""
+    lvl = np.zeros((max_out, N), np.int8)
+    idx = np.zeros((max_out, N), np.int32)
+    M = load().ens_sg_initial(int(N), int(level), int(max_out), lvl, idx)
+    if M < 0:
+        raise EnsError(f"ens_sg_initial failed ({M})")
+    return lvl[:M].copy(), idx[:M].copy()

@@ -1,0 +1,178 @@
+"""The grid-generation and grouping loop of Section 3.1 ("The algorithm",
+steps 1-4 of the flowchart) on the GPU path.
+
+    Y_0 = initial sparse grid (levels 0..init_level), grouped in generation order
+    loop:
+      1. solve the newest points in ensembles -> G(y) = ||u||_2^2, I(y) = iterations
+      2. surpluses of G and I at the new points (ens_sg_eval with values)
+      3. refine the new points whose |surplus of G| >= tau (ens_sg_refine, host);
+         stop when nothing is refined or |Y| + |Y_new| > n_max
+      4. group the new points by the iteration surrogate (ens_group) and go to 1.
+
+Groupings: "sur" (the surrogate, Section 3.1), "nat" (generation order), "rand"
+(a seeded permutation), all with S-sample ensembles; "its" (sorted by the
+actual counts, known only afterwards) is reported through R only.
+
+The grid table (levels, indices, surpluses) stays on the device in generation
+order; per level the host reads back only the G surpluses it refines on.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import ens, inputs
+from .solver import EnsembleSolver
+
+
+def coords(lvl: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """y_{l,i} = i 2^(1-l) - 1 (exact: dyadic)."""
+    return idx.astype(np.float64) * np.exp2(1.0 - lvl.astype(np.float64)) - 1.0
+
+
+def work_ratio(S: int, perm: np.ndarray, iters: np.ndarray) -> float:
+    """Eq. (R): S sum_k max_{i in k} I_i / sum_i I_i over the real samples."""
+    it = np.asarray(iters, np.float64)[perm]
+    num = sum(float(it[k:k + S].max()) for k in range(0, len(it), S))
+    return S * num / float(it.sum())
+
+
+class Adaptive:
+    """Runs the loop for one workload with one grouping."""
+
+    def __init__(self, handle: ens.Handle, wl: inputs.Workload, S: int | None = None,
+                 solver: EnsembleSolver | None = None, per_sample: bool = False):
+        self.h = handle
+        self.wl = wl
+        self.S = wl.S if S is None else S
+        self.per_sample = per_sample
+        self.prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+        cap = min(wl.n_max, 16384)
+        if solver is None:
+            solver = EnsembleSolver(handle, self.prob, 1 if per_sample else self.S,
+                                    1 if per_sample else cap, wl.rtol, wl.maxit)
+        self.solver = solver
+        self.dev = solver.dev
+        self.launches = 0
+        self.solve_sets = []
+
+    def _solve(self, y_dev: torch.Tensor, order: torch.Tensor, offset: int):
+        """Solve the points y_dev[order] and return (G, I) in point order.
+        Records which global points each solve call held (for launch counts)."""
+        M = y_dev.shape[0]
+        G = torch.empty(M, dtype=torch.float64, device=self.dev)
+        I = torch.empty(M, dtype=torch.float64, device=self.dev)
+        xi = y_dev.index_select(0, order)
+        if self.per_sample:
+            order_h = order.cpu().numpy()
+            for j in range(M):
+                it, st, rr, q = self.solver.solve(xi[j:j + 1])
+                G[order[j:j + 1]] = q
+                I[order[j:j + 1]] = it.to(torch.float64)
+                self.solve_sets.append(np.array([offset + order_h[j]]))
+        else:
+            it, st, rr, q = self.solver.solve(xi)
+            G[order] = q
+            I[order] = it.to(torch.float64)
+            self.solve_sets.append(np.arange(offset, offset + M))
+        return G, I
+
+    def kernel_launches(self, I: np.ndarray) -> int:
+        """Kernels of libens launched by the last run: per solve call assembly,
+        PCG init, three kernels per device-loop trip, finish and QoI; plus the
+        grouping and surplus kernels counted in run()."""
+        n = self.launches
+        for pts in self.solve_sets:
+            n += 4 + 3 * max(1, int(I[pts].max()))
+        return n
+
+    def run(self, grouping: str = "sur", seed: int = 0, record_trips: bool = False):
+        wl, S, dev = self.wl, self.S, self.dev
+        N = wl.nparam
+        self.launches = 0
+        self.solve_sets = []
+        lvl, idx = ens.ens_sg_initial(N, wl.init_level)
+        y = coords(lvl, idx)
+        lvl_d = torch.from_numpy(lvl).to(dev)
+        idx_d = torch.from_numpy(idx).to(dev)
+        y_d = torch.from_numpy(y).to(dev)
+        M0 = len(lvl)
+        order = torch.arange(M0, device=dev)
+        G, I = self._solve(y_d, order, 0)
+        # surpluses of the initial grid, one level at a time (Eq. hierSGint)
+        cG = torch.empty(M0, dtype=torch.float64, device=dev)
+        cI = torch.empty(M0, dtype=torch.float64, device=dev)
+        lev = lvl.sum(axis=1)
+        for L in range(int(lev.max()) + 1):
+            a, b = int(np.searchsorted(lev, L, "left")), int(np.searchsorted(lev, L, "right"))
+            if b > a:
+                ens.ens_sg_eval(self.h, lvl_d[:a] if a else None, idx_d[:a], cG[:a], y_d[a:b], cG[a:b],
+                                values=G[a:b])
+                ens.ens_sg_eval(self.h, lvl_d[:a] if a else None, idx_d[:a], cI[:a], y_d[a:b], cI[a:b],
+                                values=I[a:b])
+                self.launches += 2
+        levels = [(0, M0)]
+        perms = [np.arange(M0, dtype=np.int32)]
+        preds = [np.zeros(M0)]
+        rng_seed = seed
+        first = 0
+        while True:
+            cG_host = cG[first:].cpu().numpy()
+            cG_all = np.concatenate([np.zeros(first), cG_host])
+            nl, ni = ens.ens_sg_refine(lvl, idx, first, cG_all, wl.tau, wl.max_level)
+            if len(nl) == 0 or len(lvl) + len(nl) > wl.n_max:
+                break
+            Mn = len(nl)
+            yn = torch.from_numpy(coords(nl, ni)).to(dev)
+            pred = torch.empty(Mn, dtype=torch.float64, device=dev)
+            if grouping == "sur":
+                perm = torch.empty(Mn, dtype=torch.int32, device=dev)
+                ens.ens_group(self.h, lvl_d, idx_d, cI, yn, S, pred, perm)
+                self.launches += 2
+            elif grouping == "nat":
+                perm = torch.arange(Mn, dtype=torch.int32, device=dev)
+            elif grouping == "rand":
+                perm = torch.from_numpy(inputs.rand_perm(Mn, rng_seed)).to(dev)
+                rng_seed += 1
+            else:
+                raise ValueError(f"unknown grouping {grouping}")
+            Gn, In = self._solve(yn, perm.to(torch.int64), len(lvl))
+            cGn = torch.empty(Mn, dtype=torch.float64, device=dev)
+            cIn = torch.empty(Mn, dtype=torch.float64, device=dev)
+            ens.ens_sg_eval(self.h, lvl_d, idx_d, cG, yn, cGn, values=Gn)
+            ens.ens_sg_eval(self.h, lvl_d, idx_d, cI, yn, cIn, values=In)
+            self.launches += 2
+            first = len(lvl)
+            levels.append((first, first + Mn))
+            perms.append(perm.cpu().numpy())
+            preds.append(pred.cpu().numpy() if grouping == "sur" else np.zeros(Mn))
+            lvl = np.concatenate([lvl, nl])
+            idx = np.concatenate([idx, ni])
+            lvl_d = torch.cat([lvl_d, torch.from_numpy(nl).to(dev)])
+            idx_d = torch.cat([idx_d, torch.from_numpy(ni).to(dev)])
+            y_d = torch.cat([y_d, yn])
+            G = torch.cat([G, Gn])
+            I = torch.cat([I, In])
+            cG = torch.cat([cG, cGn])
+            cI = torch.cat([cI, cIn])
+        return dict(lvl=lvl, idx=idx, y=y_d.cpu().numpy(), G=G.cpu().numpy(), I=I.cpu().numpy(),
+                    cG=cG.cpu().numpy(), cI=cI.cpu().numpy(), levels=levels, perms=perms, preds=preds,
+                    S=S)
+
+
+def ratios(run: dict, S: int | None = None):
+    """R_l per level and R overall (Eqs. Rl, R) for the run's grouping and for
+    the iteration-sorted ("its") grouping of the same levels."""
+    S = run["S"] if S is None else S
+    out = {}
+    for name in ("run", "its"):
+        Rl, num, den = [], 0.0, 0.0
+        for (a, b), perm in zip(run["levels"], run["perms"]):
+            it = run["I"][a:b]
+            p = np.argsort(it, kind="stable") if name == "its" else perm
+            r = work_ratio(S, p, it)
+            Rl.append(r)
+            num += r * it.sum() / S
+            den += it.sum()
+        out[name] = (Rl, S * num / den)
+    return out

@@ -1,0 +1,90 @@
+"""The C ABI builds, loads and exports every entry point include/ens.h declares,
+and its host-only routines (grid bookkeeping, sizes) agree with the oracle.
+CPU only: no compute call touches a GPU here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1705_02003_gb300 import build, ens, inputs, uq
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ens.h")
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ens_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = ens.load()
+    names = declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(ens.EXPORTS)
+
+
+def test_build_is_for_sm_103a():
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    assert os.path.exists(build.build())
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = ens.load().ens_create(ctypes.byref(h), 0)
+    assert rc in (ens.ECUDA, ens.EINVAL) and not h.value
+
+
+@pytest.mark.parametrize("wl", list(inputs.WORKLOADS.values()), ids=lambda w: w.name)
+def test_problem_sizes_match_oracle(wl):
+    p = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    kind = {"fd5": O.FD5_LOGKL, "q1": O.Q1_ROT, "fd7": O.FD7_AXIS}[wl.kind]
+    assert ens.ens_problem_size(p) == O.problem_size(kind, wl.n)
+
+
+def test_problem_validation():
+    with pytest.raises(ens.EnsError):
+        ens.ens_problem_size(ens.problem("q1", 16, 3, 4.0))  # Q1 needs N = 4
+    with pytest.raises(ens.EnsError):
+        ens.ens_problem_size(ens.problem("fd5", 1, 2, 3.0))
+    with pytest.raises(ens.EnsError):
+        ens.ens_problem_size(ens.problem(9, 16, 2, 3.0))
+    assert ens.load().ens_pcg_workspace_size(1024, 4992, 3, 1) == 0  # S must be a power of two
+
+
+@pytest.mark.parametrize("N,L", [(1, 6), (2, 4), (4, 2), (6, 2), (8, 1)])
+def test_initial_grid_bit_exact(N, L):
+    a = ens.ens_sg_initial(N, L)
+    b = O.sg_initial(N, L)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    np.testing.assert_array_equal(uq.coords(*a), O.sg_points(*b))
+
+
+def test_refinement_bit_exact():
+    rng = np.random.default_rng(9)
+    for N in (2, 3, 4, 6):
+        lvl, idx = O.sg_initial(N, 2)
+        for trial in range(3):
+            sur = rng.standard_normal(len(lvl))
+            first = int(rng.integers(0, len(lvl)))
+            for tau, cap in [(0.5, 10), (0.0, 3), (2.0, 10)]:
+                got = ens.ens_sg_refine(lvl, idx, first, sur, tau, cap)
+                want = O.sg_refine(lvl, idx, first, sur, tau, cap)
+                assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+def test_work_ratio_matches_oracle():
+    rng = np.random.default_rng(10)
+    for S in (1, 4, 8, 16):
+        it = rng.integers(1, 500, 77).astype(np.float64)
+        p = rng.permutation(77).astype(np.int32)
+        assert uq.work_ratio(S, p, it) == pytest.approx(O.work_ratio(S, p, it), rel=1e-14)

@@ -1,0 +1,144 @@
+"""GPU parity of the grouping step (K6 surrogate, K7 sort-and-chunk) and of the
+whole adaptive loop against the oracle.  Predictions and permutations are
+compared bit for bit when both sides are fed the same grid and iteration
+counts."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import uq as ouq
+from paper_1705_02003_gb300 import ens, inputs, uq
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h(ens_lib):
+    return ens.Handle(0)
+
+
+def dev(a, dt=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return (t if dt is None else t.to(dt)).cuda()
+
+
+@pytest.fixture(scope="module")
+def small_run():
+    """The oracle's adaptive loop on the 32 x 32 5-point workload."""
+    wl = inputs.WORKLOADS["fd5_32_adaptive"]
+
+    def solve(y):
+        out = O.solve_batch(O.FD5_LOGKL, wl.n, wl.nparam, wl.aniso, y, wl.rtol, wl.maxit, nthreads=8)
+        return out["G"], out["iters"]
+
+    return ouq.adaptive(solve, N=2, S=wl.S, tau=wl.tau, init_level=wl.init_level, max_level=wl.max_level,
+                        n_max=wl.n_max)
+
+
+def synthetic_grid(N, levels, seed):
+    """A larger refined grid from an analytic function (no PDE solves)."""
+    rng = np.random.default_rng(seed)
+    lvl, idx = O.sg_initial(N, 1)
+    y = O.sg_points(lvl, idx)
+    f = lambda Y: np.exp(-np.sum((Y - 0.3) ** 2, axis=1) * 3.0) + 0.1 * Y[:, 0]
+    c = ouq.hierarchize(lvl, idx, f(y))
+    first = 0
+    for _ in range(levels):
+        nl, ni = O.sg_refine(lvl, idx, first, c, 1e-3, 64)
+        if not len(nl):
+            break
+        yn = O.sg_points(nl, ni)
+        cn = f(yn) - O.sg_eval(lvl, idx, c, yn)
+        first = len(lvl)
+        lvl, idx, c = np.concatenate([lvl, nl]), np.concatenate([idx, ni]), np.concatenate([c, cn])
+    # iteration-like surpluses: integers with structure
+    cI = np.round(rng.standard_normal(len(lvl)) * 20.0)
+    return lvl, idx, cI
+
+
+def test_surrogate_and_grouping_bit_exact_on_the_oracle_run(h, small_run):
+    r = small_run
+    for (a, b), pred_o, perm_o in zip(r["levels"][1:], r["pred"][1:], r["perms"]["sur"][1:]):
+        yq = O.sg_points(r["lvl"][a:b], r["idx"][a:b])
+        pred = torch.empty(b - a, dtype=torch.float64, device="cuda")
+        perm = torch.empty(b - a, dtype=torch.int32, device="cuda")
+        n_ens = ens.ens_group(h, dev(r["lvl"][:a]), dev(r["idx"][:a]), dev(r["cI"][:a]), dev(yq), r["S"], pred,
+                              perm)
+        assert n_ens == -(-(b - a) // r["S"])
+        assert np.array_equal(pred.cpu().numpy(), pred_o)
+        assert np.array_equal(perm.cpu().numpy(), perm_o)
+        # surpluses of the new points through the values form
+        cI = torch.empty(b - a, dtype=torch.float64, device="cuda")
+        ens.ens_sg_eval(h, dev(r["lvl"][:a]), dev(r["idx"][:a]), dev(r["cI"][:a]), dev(yq), cI,
+                        values=dev(r["I"][a:b]))
+        assert np.array_equal(cI.cpu().numpy(), r["cI"][a:b])
+
+
+@pytest.mark.parametrize("N,levels,Mq", [(4, 4, 500), (2, 7, 2000), (6, 3, 4096), (8, 2, 333)])
+def test_surrogate_bit_exact_on_larger_grids(h, N, levels, Mq):
+    lvl, idx, cI = synthetic_grid(N, levels, seed=N)
+    rng = np.random.default_rng(N + 1)
+    yq = rng.uniform(-1, 1, (Mq, N))
+    yq[: Mq // 4] = np.round(yq[: Mq // 4] * 64) / 64  # dyadic points hit basis kinks exactly
+    want = O.sg_eval(lvl, idx, cI, yq)
+    pred = torch.empty(Mq, dtype=torch.float64, device="cuda")
+    perm = torch.empty(Mq, dtype=torch.int32, device="cuda")
+    ens.ens_group(h, dev(lvl), dev(idx), dev(cI), dev(yq), 16, pred, perm)
+    assert np.array_equal(pred.cpu().numpy(), want)
+    assert np.array_equal(perm.cpu().numpy(), O.sort_perm(want))
+
+
+@pytest.mark.parametrize("Mq", [1, 2, 3, 31, 1000, 4097, 16384])
+def test_sort_chunk_matches_stable_sort(h, Mq):
+    rng = np.random.default_rng(Mq)
+    keys = rng.integers(0, 40, Mq).astype(np.float64)  # many ties
+    keys[rng.random(Mq) < 0.1] = -0.0
+    perm = torch.empty(Mq, dtype=torch.int32, device="cuda")
+    n_ens = ens.ens_sort_chunk(h, dev(keys), 8, perm)
+    assert n_ens == -(-Mq // 8)
+    assert np.array_equal(perm.cpu().numpy(), O.sort_perm(keys))
+
+
+def test_sort_puts_nan_last_and_rejects_oversize(h):
+    keys = np.array([3.0, np.nan, 1.0, np.inf, -np.inf, np.nan, 1.0])
+    perm = torch.empty(7, dtype=torch.int32, device="cuda")
+    ens.ens_sort_chunk(h, dev(keys), 2, perm)
+    assert perm.cpu().numpy().tolist() == [4, 2, 6, 0, 3, 1, 5]
+    big = torch.zeros(16385, dtype=torch.float64, device="cuda")
+    with pytest.raises(ens.EnsError):
+        ens.ens_sort_chunk(h, big, 2, torch.empty(16385, dtype=torch.int32, device="cuda"))
+
+
+def test_qoi_matches_definition(h):
+    rng = np.random.default_rng(3)
+    E, J, S = 3, 1000, 8
+    x = rng.standard_normal((E, J, S))
+    w = rng.random(J)
+    out = torch.empty(E * S, dtype=torch.float64, device="cuda")
+    ens.ens_qoi(h, J, S, E, dev(x.ravel()), out)
+    np.testing.assert_allclose(out.cpu().numpy(), (x**2).sum(axis=1).ravel(), rtol=1e-13)
+    ens.ens_qoi(h, J, S, E, dev(x.ravel()), out, w=dev(w))
+    np.testing.assert_allclose(out.cpu().numpy(), np.einsum("j,ejs->es", w, x).ravel(), rtol=1e-12)
+
+
+def test_adaptive_loop_matches_oracle(h, small_run):
+    """The whole flowchart loop on the GPU path: same grid, iteration counts
+    within one, G within 1e-10, and R of each level from the run's groups."""
+    wl = inputs.WORKLOADS["fd5_32_adaptive"]
+    ad = uq.Adaptive(h, wl)
+    run = ad.run("sur")
+    r = small_run
+    assert np.array_equal(run["lvl"], r["lvl"]) and np.array_equal(run["idx"], r["idx"])
+    assert run["levels"] == r["levels"]
+    assert np.max(np.abs(run["I"] - r["I"])) <= 1
+    np.testing.assert_allclose(run["G"], r["G"], rtol=1e-10)
+    if np.array_equal(run["I"], r["I"]):
+        for p, po in zip(run["perms"][1:], r["perms"]["sur"][1:]):
+            assert np.array_equal(p, po)
+    R = uq.ratios(run)
+    Ro = ouq.ratios(r)
+    if np.array_equal(run["I"], r["I"]):
+        np.testing.assert_allclose(R["run"][0], Ro["sur"][0], rtol=1e-12)
+    for lev, (a, b) in enumerate(run["levels"]):
+        assert R["run"][0][lev] >= 1.0

@@ -1,0 +1,362 @@
+"""Benchmark: sample-solves/s of the surrogate-grouped ensemble PCG.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload q1_256_adaptive] [--no-arms]
+
+A step is one pass of the whole path over the workload: the grid-generation
+and grouping loop of the paper's flowchart (initial sparse grid, then per
+level: surrogate grouping (K6, K7), ensemble assembly (K1), ensemble Jacobi-PCG
+(K2-K4) to rel. residual 1e-8, QoI, surpluses and host refinement) until the
+sample budget is reached.  value = samples solved / device time (CUDA events
+around K steps, max over ranks).  The same run reports the natural-order and
+random groupings, one-sample-at-a-time PCG on the same GPU, the ensemble SpMV
+kernel against the HBM roofline, an end-to-end figure through the public API
+with host buffers, and the CPU oracle on a bounded sample of the same points.
+
+--impl reference times the CPU oracle (the reference arm of this project) on
+the host cores for the same metric.  Multi-GPU runs are independent replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sample-solves/s at rel-res 1e-8: ensemble PCG vs per-sample PCG; SpMV HBM GB/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def allmax(pg, v):
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+OKINDS = {"fd5": 1, "q1": 2, "fd7": 3}
+
+
+def oracle_rate(wl, points: np.ndarray, threads: int):
+    import oracle as O
+
+    t0 = time.perf_counter()
+    out = O.solve_batch(OKINDS[wl.kind], wl.n, wl.nparam, wl.aniso, points, wl.rtol, wl.maxit, nthreads=threads)
+    dt = time.perf_counter() - t0
+    assert np.all(out["status"] == O.CONVERGED)
+    return len(points) / dt, dt, out
+
+
+def oracle_sample_points(wl, count: int):
+    """A bounded, deterministic sample of the workload's points: every k-th
+    point of the full sparse grid of the workload's dimension (levels 0..3)."""
+    from paper_1705_02003_gb300 import ens, uq
+
+    lvl, idx = ens.ens_sg_initial(wl.nparam, 3)
+    y = uq.coords(lvl, idx)
+    step = max(1, len(y) // count)
+    return y[::step][:count]
+
+
+def run_reference(args, wl):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    pts = oracle_sample_points(wl, args.ref_samples)
+    for _ in range(args.warmup):
+        oracle_rate(wl, pts[: max(1, threads)], threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(wl, pts, threads)
+    dt = time.perf_counter() - t0
+    value = len(pts) * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sample-solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "kind": wl.kind, "n": wl.n, "N": wl.nparam, "rtol": wl.rtol,
+                   "sample": f"{len(pts)} sparse-grid points per step"},
+        "cpu_baseline": {"value": value, "unit": "sample-solves/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{len(pts)} points of the level-3 sparse grid, one sample per thread"},
+        "e2e": {"value": value, "unit": "sample-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, wl):
+    import torch
+
+    from paper_1705_02003_gb300 import ens
+    from paper_1705_02003_gb300.uq import Adaptive, ratios
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    h = ens.Handle(local)
+    stream = torch.cuda.current_stream()
+    ad = Adaptive(h, wl)
+
+    # warm-up (also fixes the grid: it does not depend on the grouping)
+    for _ in range(max(args.warmup, 1)):
+        run = ad.run("sur")
+    torch.cuda.synchronize()
+    M = len(run["I"])
+    launches_per_step = ad.kernel_launches(run["I"])
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(pg)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        run = ad.run("sur")
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    tmax = allmax(pg, t)
+    value = world * M * args.steps / tmax
+    R = ratios(run)
+
+    extra = {}
+    if not args.no_arms:
+        # the other groupings and one-sample-at-a-time PCG, one step each
+        for arm in ("nat", "rand"):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r2 = ad.run(arm, seed=0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ta = e0.elapsed_time(e1) / 1e3
+            extra[arm] = {"value": M / ta, "R": ratios(r2)["run"][1]}
+        ps = Adaptive(h, wl, per_sample=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ps.run("nat")  # warm-up (graph instantiation)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r3 = ps.run("nat")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1) / 1e3
+        extra["per_sample"] = {"value": M / tp, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r3["I"] - run["I"])))}
+
+    # dominant kernel: the ensemble SpMV (K2) on a full-capacity batch
+    sol = ad.solver
+    E = sol.Emax
+    L = E * sol.S
+    xi_all = torch.from_numpy(run["y"][:L] if len(run["y"]) >= L else
+                              np.resize(run["y"], (L, wl.nparam))).to("cuda")
+    ens.ens_assemble(h, sol.prob, sol.S, E, xi_all.reshape(-1).contiguous(), sol.rowptr, sol.colidx, sol.vals,
+                     sol.dinv, sol.b)
+    p = sol.b
+    q = torch.empty_like(sol.x)
+    pq = torch.empty(L, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ens.ens_spmv(h, sol.J, sol.nnz, sol.S, E, sol.rowptr, sol.colidx, sol.vals, p, q, pq, sol.work)
+    reps = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ens.ens_spmv(h, sol.J, sol.nnz, sol.S, E, sol.rowptr, sol.colidx, sol.vals, p, q, pq, sol.work)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_spmv = e0.elapsed_time(e1) / 1e3 / reps
+    spmv_bytes = E * (8 * sol.nnz * sol.S + 4 * sol.nnz + 4 * (sol.J + 1) + 16 * sol.J * sol.S)
+    peak, peak_kind = peaks()
+    achieved = spmv_bytes / t_spmv / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_spmv (K2)", "peak_source": peak_kind,
+                "bytes_per_launch": spmv_bytes, "launch_ms": t_spmv * 1e3}
+
+    # end to end through the public API with host buffers: the loop copies each
+    # level's points in and its surpluses out; in addition every solve's
+    # solution fields u (all samples) go to pinned host memory, and the
+    # per-sample G, I and surpluses come back at the end of the step
+    host_u = torch.empty(max(M, sol.S) * sol.J + sol.Emax * sol.S * sol.J, dtype=torch.float64,
+                         pin_memory=True)
+    moved = {"d2h": 0}
+    cursor = {"at": 0}
+
+    def sink(s_, m):
+        E_ = math.ceil(m / s_.S)
+        n = E_ * s_.J * s_.S
+        if cursor["at"] + n > host_u.numel():
+            cursor["at"] = 0
+        host_u[cursor["at"]:cursor["at"] + n].copy_(s_.x[:n], non_blocking=True)
+        cursor["at"] += n
+        moved["d2h"] += 8 * n
+
+    ad.sink = sink
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cursor["at"] = 0
+        r4 = ad.run("sur")
+        torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    ad.sink = None
+    N_ = wl.nparam
+    h2d = int(M * N_ * (8 + 1 + 4))                      # point coordinates, levels, indices
+    d2h = int(moved["d2h"] / args.steps) + int(M * 8 * 2 + M * 8 * 4)  # u fields, surpluses, G/I/cG/cI
+    e2e = {"value": world * M * args.steps / allmax(pg, te), "unit": "sample-solves/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        pts = run["y"][:: max(1, M // args.cpu_samples)][: args.cpu_samples]
+        rate, dt, _ = oracle_rate(wl, pts, threads)
+        cpu = {"value": rate, "unit": "sample-solves/s", "cores": threads, "kind": "oracle",
+               "sample": f"{len(pts)} of the {M} grid points (every {max(1, M // args.cpu_samples)}-th), "
+                         f"FP64 per-sample Jacobi-PCG, one sample per thread, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "sample-solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "kind": wl.kind, "n": wl.n, "J": sol.J, "nnz": sol.nnz,
+                       "N": wl.nparam, "S": sol.S, "samples_per_step": M, "levels": len(run["levels"]),
+                       "rtol": wl.rtol, "grouping": "sur", "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (vals of one level >= 225 MB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "R": {"sur": R["run"][1], "its": R["its"][1]},
+            "arms": extra,
+        }
+        if "per_sample" in extra:
+            line["speedup_vs_per_sample"] = value / extra["per_sample"]["value"]
+        # roofline of the whole solve: frozen lanes stream their values too
+        print(json.dumps(line))
+    h.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="q1_256_adaptive")
+    ap.add_argument("--no-arms", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-samples", type=int, default=32)
+    ap.add_argument("--ref-samples", type=int, default=32)
+    args = ap.parse_args()
+    from paper_1705_02003_gb300 import inputs
+
+    wl = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

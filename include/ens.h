@@ -126,6 +126,15 @@ int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   double rtol, int maxit, int32_t *iters, double *relres, int32_t *status,
                   void *work, size_t work_bytes, void *stream);
 
+/* Ensemble SpMV (Section 2.3: the matrix-vector product of the commuted
+ * Kronecker system, each nonzero's S values applied to the S lanes of its
+ * column): q[E][J][S] = A_s p_s for every lane, and pq[E][S] = p_s^T q_s
+ * (device, may be NULL).  This is the same kernel the PCG loop runs (K2),
+ * launched alone; work as for ens_pcg_solve. */
+int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const int32_t *rowptr,
+             const int32_t *colidx, const double *vals, const double *p, double *q, double *pq,
+             void *work, size_t work_bytes, void *stream);
+
 /* Surrogate-based grouping (Section 3.1, "SGS-based grouping", Eq. SGSiterations):
  * evaluates the hierarchical piecewise-linear sparse-grid surrogate
  *   pred[q] = sum_{m<M} surplus[m] prod_n psi_{lvl[m][n], idx[m][n]}(yq[q][n])

@@ -58,6 +58,7 @@ struct Args {
     int32_t *iters, *status;
     double *relres;
     Ws w;
+    double *pq_out;  // ens_spmv: write p^T q per lane here instead of alpha
     cudaGraphConditionalHandle cond;
 };
 
@@ -339,7 +340,9 @@ __global__ void __launch_bounds__(kBlock) k_spmv(Args a)
     if (threadIdx.x == 0) dead = 0;
     double *parts[1] = {a.w.part0};
     if (!reduce_lanes<S, 1>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_SPMV, tot)) return;
-    if (threadIdx.x < S) {
+    if (threadIdx.x < S && a.pq_out) {
+        a.pq_out[e * S + threadIdx.x] = tot[threadIdx.x];
+    } else if (threadIdx.x < S) {
         const int L = e * S + threadIdx.x;
         if (a.w.live[L]) {
             const double pq = tot[threadIdx.x];
@@ -484,6 +487,34 @@ __global__ void k_finish(Args a)
         a.status[L] = ENS_LANE_MAXIT;
         a.iters[L] = a.w.k[L];
         a.relres[L] = sqrt(a.w.rr[L]) / a.w.bnorm[L];
+    }
+}
+
+// ens_spmv: every lane live, every ensemble live.
+__global__ void k_spmv_prep(Args a)
+{
+    int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L < a.E * a.S) a.w.live[L] = 1;
+    if (L < a.E) a.w.ens_live[L] = a.S;
+}
+
+template <int S>
+void launch_spmv(const Args &a, cudaStream_t st)
+{
+    dim3 grid(a.g.nblk, a.E);
+    k_spmv<S><<<grid, kBlock, 0, st>>>(a);
+}
+
+void dispatch_spmv(const Args &a, cudaStream_t st)
+{
+    switch (a.S) {
+    case 1: launch_spmv<1>(a, st); break;
+    case 2: launch_spmv<2>(a, st); break;
+    case 4: launch_spmv<4>(a, st); break;
+    case 8: launch_spmv<8>(a, st); break;
+    case 16: launch_spmv<16>(a, st); break;
+    case 32: launch_spmv<32>(a, st); break;
+    default: launch_spmv<64>(a, st); break;
     }
 }
 
@@ -658,6 +689,37 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
     ENS_CUDA_CHECK(h, cudaGraphLaunch(exec, st));
     k_finish<<<(E * S + 255) / 256, 256, 0, st>>>(a);
     ENS_LAUNCH_CHECK(h, "ens_pcg_solve: finish kernel");
+    return ENS_OK;
+}
+
+extern "C" int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const int32_t *rowptr,
+                        const int32_t *colidx, const double *vals, const double *p, double *q, double *pq,
+                        void *work, size_t work_bytes, void *stream)
+{
+    if (!h) return ENS_EINVAL;
+    if (!lane_count_ok(S)) return set_error(h, ENS_EINVAL, "ens_spmv: S must be 1,2,4,...,64");
+    if (J <= 0 || nnz <= 0 || E < 0 || nnz >= (1LL << 31)) return set_error(h, ENS_EINVAL, "ens_spmv: bad sizes");
+    if (E == 0) return ENS_OK;
+    if (!rowptr || !colidx || !vals || !p || !q || !work) return set_error(h, ENS_EINVAL, "ens_spmv: null pointer");
+    if (((uintptr_t)vals | (uintptr_t)p | (uintptr_t)q | (uintptr_t)work) & 15)
+        return set_error(h, ENS_EINVAL, "ens_spmv: arrays must be 16-byte aligned");
+    Geo g = geometry(J, S);
+    const size_t need = layout(J, S, E, g, nullptr, nullptr);
+    if (work_bytes < need) return set_error(h, ENS_ENOMEM, "ens_spmv: workspace too small");
+    Args a;
+    memset(&a, 0, sizeof(a));
+    a.J = J; a.S = S; a.E = E; a.nnz = nnz; a.g = g;
+    a.rowptr = rowptr; a.colidx = colidx; a.vals = vals;
+    layout(J, S, E, g, &a.w, (char *)work);
+    a.w.p = const_cast<double *>(p);
+    a.w.q = q;
+    a.pq_out = pq ? pq : a.w.alpha;
+    cudaStream_t st = (cudaStream_t)stream;
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
+    k_spmv_prep<<<(E * S + 255) / 256, 256, 0, st>>>(a);
+    ENS_LAUNCH_CHECK(h, "ens_spmv: prep");
+    dispatch_spmv(a, st);
+    ENS_LAUNCH_CHECK(h, "ens_spmv: kernel");
     return ENS_OK;
 }
 

@@ -23,7 +23,7 @@ LANE_CONVERGED, LANE_MAXIT, LANE_BREAKDOWN, LANE_BADINPUT, LANE_INACTIVE = 0, 1,
 
 EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "ens_pattern",
            "ens_assemble", "ens_pcg_workspace_size", "ens_pcg_solve", "ens_group", "ens_sort_chunk",
-           "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi")
+           "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv")
 
 _lib = None
 _lock = threading.Lock()
@@ -75,6 +75,7 @@ def _declare(L):
     L.ens_sort_chunk.argtypes = [vp, c.c_int, vp, c.c_int, vp, c.POINTER(c.c_int), vp]
     L.ens_sg_eval.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_int, vp, vp, vp, vp]
     L.ens_qoi.argtypes = [vp, c.c_int, c.c_int, c.c_int, vp, vp, vp, vp]
+    L.ens_spmv.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp, c.c_size_t, vp]
     i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -204,6 +205,19 @@ def ens_pcg_solve(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx, v
                               int(maxit), _ptr(iters), _ptr(relres), _ptr(status), _ptr(work),
                               work.numel(), _stream(stream))
     h.check(rc, "ens_pcg_solve")
+
+
+def ens_spmv(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx, vals, p, q, pq, work, stream=None):
+    """q = A p per lane (and pq = p^T q per lane): the PCG loop's SpMV kernel alone."""
+    for t, nm in ((vals, "vals"), (p, "p"), (q, "q")):
+        _check_dtype(t, torch.float64, nm)
+    if pq is not None:
+        _check_dtype(pq, torch.float64, "pq")
+    if vals.numel() != E * nnz * S or p.numel() != E * J * S or q.numel() != E * J * S:
+        raise ValueError("array sizes do not match E, J, nnz, S")
+    rc = load().ens_spmv(h.ptr, int(J), int(nnz), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                         _ptr(p), _ptr(q), _ptr(pq), _ptr(work), work.numel(), _stream(stream))
+    h.check(rc, "ens_spmv")
 
 
 def ens_group(h: Handle, lvl, idx, surplus, yq, S: int, pred, perm, stream=None) -> int:

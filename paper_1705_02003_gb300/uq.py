@@ -55,6 +55,7 @@ class Adaptive:
         self.dev = solver.dev
         self.launches = 0
         self.solve_sets = []
+        self.sink = None  # optional callable(solver, M) run after every solve call
 
     def _solve(self, y_dev: torch.Tensor, order: torch.Tensor, offset: int):
         """Solve the points y_dev[order] and return (G, I) in point order.
@@ -67,11 +68,15 @@ class Adaptive:
             order_h = order.cpu().numpy()
             for j in range(M):
                 it, st, rr, q = self.solver.solve(xi[j:j + 1])
+                if self.sink:
+                    self.sink(self.solver, 1)
                 G[order[j:j + 1]] = q
                 I[order[j:j + 1]] = it.to(torch.float64)
                 self.solve_sets.append(np.array([offset + order_h[j]]))
         else:
             it, st, rr, q = self.solver.solve(xi)
+            if self.sink:
+                self.sink(self.solver, M)
             G[order] = q
             I[order] = it.to(torch.float64)
             self.solve_sets.append(np.arange(offset, offset + M))

@@ -231,5 +231,30 @@ def test_argument_errors(h):
         ens.ens_pcg_solve(h, J, nnz, 8, E, c.rowptr, c.colidx, c.vals, c.dinv, c.b, x, None, -1.0, 10, it, rr,
                           st, small)
     with pytest.raises(ens.EnsError):
-        ens.ens_assemble(h, ens.problem("fd5", 16, 2, 3.0), 3, 1, c.xi[:6], c.rowptr, c.colidx,
+        ens.ens_assemble(h, ens.problem("fd5", 16, 2, 3.0), 3, 1, c.xi[:3], c.rowptr, c.colidx,
                          torch.empty(3 * nnz, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("kind,n,N,aniso,S,M", [("q1", 30, 4, 4.0, 16, 20), ("fd7", 9, 6, 3.0, 8, 9),
+                                                ("fd5", 20, 8, 3.0, 1, 3), ("fd5", 12, 2, 3.0, 64, 64)])
+def test_spmv_bit_exact_and_lane_dots(h, kind, n, N, aniso, S, M):
+    """K2 alone: each row sum is taken in column order with separately rounded
+    products and sums, exactly as the oracle's loop, so q is bit-identical.
+    Matrix values and p come from the oracle side and are uploaded."""
+    xi = inputs.draws(M, N, seed=21)
+    c = Case(h, kind, n, N, aniso, S, xi)
+    rng = np.random.default_rng(22)
+    rp, ci = O.pattern(OKIND[kind], n)
+    V = np.stack([O.assemble(OKIND[kind], n, N, aniso, c.xi_h[L], rp, ci)[0] for L in range(c.E * S)])
+    vals = torch.from_numpy(V.reshape(c.E, S, c.nnz).transpose(0, 2, 1).copy()).cuda().reshape(-1)
+    P = rng.standard_normal((c.E * S, c.J))
+    p = torch.from_numpy(P.reshape(c.E, S, c.J).transpose(0, 2, 1).copy()).cuda().reshape(-1)
+    q = torch.empty_like(p)
+    pq = torch.empty(c.E * S, dtype=torch.float64, device="cuda")
+    work = torch.empty(ens.ens_pcg_workspace_size(c.J, c.nnz, S, c.E), dtype=torch.uint8, device="cuda")
+    ens.ens_spmv(h, c.J, c.nnz, S, c.E, c.rowptr, c.colidx, vals, p, q, pq, work)
+    Q = c.lane_vec(q)
+    for L in range(c.E * S):
+        ref = O.spmv(rp, ci, V[L], P[L])
+        assert np.array_equal(Q[L], ref)
+        assert pq[L].item() == pytest.approx(float(P[L] @ ref), rel=1e-12)

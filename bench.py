@@ -338,6 +338,43 @@ def run_ours(args, wl):
     return 0
 
 
+def run_kernel_only(args, wl):
+    """A small case of the dominant kernel for profilers: E ensembles of the
+    workload's problem (inputs larger than L2, a few GB at most), assembled once,
+    then ens_spmv launched --steps times."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens, inputs
+    from paper_1705_02003_gb300.solver import EnsembleSolver
+
+    h = ens.Handle(0)
+    prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    S = wl.S
+    E = args.kernel_ensembles
+    sol = EnsembleSolver(h, prob, S, E * S, wl.rtol, wl.maxit)
+    xi = torch.from_numpy(inputs.draws(E * S, wl.nparam, seed=1)).cuda()
+    ens.ens_assemble(h, prob, S, E, xi.reshape(-1), sol.rowptr, sol.colidx, sol.vals, sol.dinv, sol.b)
+    q = torch.empty_like(sol.x)
+    pq = torch.empty(E * S, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ens.ens_spmv(h, sol.J, sol.nnz, S, E, sol.rowptr, sol.colidx, sol.vals, sol.b, q, pq, sol.work)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ens.ens_spmv(h, sol.J, sol.nnz, S, E, sol.rowptr, sol.colidx, sol.vals, sol.b, q, pq, sol.work)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    byts = E * (8 * sol.nnz * S + 4 * sol.nnz + 4 * (sol.J + 1) + 16 * sol.J * S)
+    peak, _ = peaks()
+    print(json.dumps({"kernel": "k_spmv", "workload": wl.name, "E": E, "S": S, "ms": t * 1e3,
+                      "bytes": byts, "GBps": byts / t / 1e9, "frac": byts / t / 1e9 / peak}))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,12 +386,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--ref-samples", type=int, default=32)
+    ap.add_argument("--kernel-only", action="store_true", help="time the ensemble SpMV alone (profiling)")
+    ap.add_argument("--kernel-ensembles", type=int, default=8)
     args = ap.parse_args()
     from paper_1705_02003_gb300 import inputs
 
     wl = inputs.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.kernel_only:
+        return run_kernel_only(args, wl)
     return run_ours(args, wl)
 
 

@@ -119,7 +119,11 @@ size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E);
  *   iters[E][S], relres[E][S], status[E][S]  outputs (relres = ||r||/||b||).
  *   work          caller scratch of at least ens_pcg_workspace_size bytes.
  * The iteration runs inside one CUDA graph with a device-evaluated while loop
- * (at most maxit trips), so the call does not synchronise the stream. */
+ * (at most maxit trips), so the call does not synchronise the stream.  With
+ * the environment variable ENS_PCG_HOST_LOOP=1 at ens_create, the same kernels
+ * are instead launched from the host, which reads the live-lane count back
+ * every 16 trips (a profiling aid: kernel profilers do not see kernels inside
+ * a conditional graph body); results are identical. */
 int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   const int32_t *rowptr, const int32_t *colidx, const double *vals,
                   const double *dinv, const double *b, double *x, const uint8_t *active,

@@ -11,6 +11,7 @@
 #include "ens_common.cuh"
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <unordered_set>
 
@@ -25,6 +26,8 @@ extern "C" int ens_create(ens_handle *out, int device)
     if (cudaSetDevice(device) != cudaSuccess) return ENS_ECUDA;
     ens_ctx *h = new ens_ctx();
     h->device = device;
+    const char *hl = getenv("ENS_PCG_HOST_LOOP");
+    h->host_loop = (hl && hl[0] == '1') ? 1 : 0;
     if (cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess) {
         delete h;
         return ENS_ECUDA;

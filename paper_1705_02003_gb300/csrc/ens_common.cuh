@@ -27,6 +27,7 @@ struct ens_ctx {
     cudaStream_t capture = nullptr;          // private stream used only to capture graphs
     std::vector<ens::GraphEntry> graphs;     // small LRU cache of instantiated loops
     uint64_t clock = 0;
+    int host_loop = 0;                       // ENS_PCG_HOST_LOOP=1: launch the PCG loop from the host
 };
 
 namespace ens {

@@ -16,6 +16,11 @@
 //       values as 16-byte vector loads), partial p^T q       -> alpha
 //   K3  x += alpha p, r -= alpha q, partial r^T r, r^T D^-1 r  -> convergence, beta
 //   K4  p = D^-1 r + beta p; block (0,0) also drives the graph's while loop.
+// Arithmetic: GB300 issues about two FP64 operations per clock per SM, which
+// is the binding limit of these kernels before HBM is, so every
+// multiply-accumulate is one fused multiply-add (the per-row sums keep the
+// oracle's column order; only the rounding of each step differs from it).
+//
 // The loop is one CUDA graph: a conditional WHILE node whose body holds K2-K4
 // and whose condition K4 sets to (live lanes > 0 && trips < maxit), so the
 // host launches one graph per solve and never waits inside it.
@@ -59,6 +64,7 @@ struct Args {
     double *relres;
     Ws w;
     double *pq_out;  // ens_spmv: write p^T q per lane here instead of alpha
+    int in_graph;    // K4 drives the graph's while loop (else the host loops)
     cudaGraphConditionalHandle cond;
 };
 
@@ -235,9 +241,9 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a)
 #pragma unroll
         for (int v = 0; v < V; v++) {
             xv.v[v] = 0.0;
-            pv.v[v] = dmul(dv.v[v], bv.v[v]);
-            acc[0][v] = dadd(acc[0][v], dmul(bv.v[v], bv.v[v]));
-            acc[1][v] = dadd(acc[1][v], dmul(bv.v[v], pv.v[v]));
+            pv.v[v] = dv.v[v] * bv.v[v];
+            acc[0][v] = fma(bv.v[v], bv.v[v], acc[0][v]);
+            acc[1][v] = fma(bv.v[v], pv.v[v], acc[1][v]);
         }
         xv.store(a.x + o);
         bv.store(a.w.r + o);
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv(Args a)
                 for (int u = 0; u < kChunk; u++)
                     if (kb + u < k1) {
 #pragma unroll
-                        for (int v = 0; v < V; v++) s[v] = dadd(s[v], dmul(av[u].v[v], xv[u].v[v]));
+                        for (int v = 0; v < V; v++) s[v] = fma(av[u].v[v], xv[u].v[v], s[v]);
                     }
             }
             Vec<V> qv, pr;
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv(Args a)
             qv.store(q + (size_t)r * S);
             pr.load(p + (size_t)r * S);
 #pragma unroll
-            for (int v = 0; v < V; v++) acc[0][v] = dadd(acc[0][v], dmul(pr.v[v], s[v]));
+            for (int v = 0; v < V; v++) acc[0][v] = fma(pr.v[v], s[v], acc[0][v]);
         }
     }
     __shared__ double tot[S];
@@ -395,10 +401,10 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a)
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 if (!lv[v]) continue;  // frozen lane: keep x and r
-                xv.v[v] = dadd(xv.v[v], dmul(al[v], pv.v[v]));
-                rv.v[v] = dsub(rv.v[v], dmul(al[v], qv.v[v]));
-                acc[0][v] = dadd(acc[0][v], dmul(rv.v[v], rv.v[v]));
-                acc[1][v] = dadd(acc[1][v], dmul(rv.v[v], dmul(dv.v[v], rv.v[v])));
+                xv.v[v] = fma(al[v], pv.v[v], xv.v[v]);
+                rv.v[v] = fma(-al[v], qv.v[v], rv.v[v]);
+                acc[0][v] = fma(rv.v[v], rv.v[v], acc[0][v]);
+                acc[1][v] = fma(rv.v[v], dv.v[v] * rv.v[v], acc[1][v]);
             }
             xv.store(a.x + o);
             rv.store(a.w.r + o);
@@ -447,7 +453,7 @@ __global__ void __launch_bounds__(kBlock) k_direction(Args a)
         const int trips = a.w.ctl[CTL_TRIPS] + 1;
         a.w.ctl[CTL_TRIPS] = trips;
         const int more = (a.w.ctl[CTL_NLIVE] > 0) && (trips < a.maxit);
-        cudaGraphSetConditional(a.cond, more ? 1u : 0u);
+        if (a.in_graph) cudaGraphSetConditional(a.cond, more ? 1u : 0u);
     }
     if (a.w.ens_live[e] == 0) return;
     const int lane0 = (threadIdx.x % TPR) * V;
@@ -472,7 +478,7 @@ __global__ void __launch_bounds__(kBlock) k_direction(Args a)
         pv.load(a.w.p + o);
 #pragma unroll
         for (int v = 0; v < V; v++)
-            if (lv[v]) pv.v[v] = dadd(dmul(dv.v[v], rv.v[v]), dmul(be[v], pv.v[v]));
+            if (lv[v]) pv.v[v] = fma(be[v], pv.v[v], dv.v[v] * rv.v[v]);
         pv.store(a.w.p + o);
     }
 }
@@ -603,6 +609,7 @@ int loop_graph(ens_ctx *h, Args a, cudaGraphExec_t *out)
     }
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     a.cond = cond;
+    a.in_graph = 1;
     e = cudaStreamBeginCaptureToGraph(h->capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
@@ -683,10 +690,23 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
     ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl, 0, CTL_WORDS * sizeof(int), st));
     dispatch_init(a, st);
     ENS_LAUNCH_CHECK(h, "ens_pcg_solve: init kernel");
-    cudaGraphExec_t exec;
-    int rc = loop_graph(h, a, &exec);
-    if (rc) return rc;
-    ENS_CUDA_CHECK(h, cudaGraphLaunch(exec, st));
+    if (h->host_loop) {
+        // Same kernels launched from the host, with the live count read back
+        // every 16 trips (profilers see each launch; the graph path does not
+        // expose kernels inside a conditional body to them).
+        int ctl[2] = {1, 0};
+        while (ctl[0] > 0 && ctl[1] < maxit) {
+            for (int t = 0; t < 16; t++) dispatch_body(a, st);
+            ENS_LAUNCH_CHECK(h, "ens_pcg_solve: loop kernels");
+            ENS_CUDA_CHECK(h, cudaMemcpyAsync(ctl, a.w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+            ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+        }
+    } else {
+        cudaGraphExec_t exec;
+        int rc = loop_graph(h, a, &exec);
+        if (rc) return rc;
+        ENS_CUDA_CHECK(h, cudaGraphLaunch(exec, st));
+    }
     k_finish<<<(E * S + 255) / 256, 256, 0, st>>>(a);
     ENS_LAUNCH_CHECK(h, "ens_pcg_solve: finish kernel");
     return ENS_OK;
@@ -738,7 +758,7 @@ __global__ void __launch_bounds__(1024) k_qoi(int J, int S, const double *__rest
     double acc = 0.0;
     for (int j = g; j < J; j += G) {
         double v = xe[(size_t)j * S + s];
-        acc = dadd(acc, w ? dmul(w[j], v) : dmul(v, v));
+        acc = fma(w ? w[j] : v, v, acc);
     }
     sh[t] = acc;
     __syncthreads();

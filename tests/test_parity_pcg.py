@@ -237,10 +237,11 @@ def test_argument_errors(h):
 
 @pytest.mark.parametrize("kind,n,N,aniso,S,M", [("q1", 30, 4, 4.0, 16, 20), ("fd7", 9, 6, 3.0, 8, 9),
                                                 ("fd5", 20, 8, 3.0, 1, 3), ("fd5", 12, 2, 3.0, 64, 64)])
-def test_spmv_bit_exact_and_lane_dots(h, kind, n, N, aniso, S, M):
-    """K2 alone: each row sum is taken in column order with separately rounded
-    products and sums, exactly as the oracle's loop, so q is bit-identical.
-    Matrix values and p come from the oracle side and are uploaded."""
+def test_spmv_matches_oracle_and_lane_dots(h, kind, n, N, aniso, S, M):
+    """K2 alone: each row sum is taken in the oracle's column order, with one
+    rounding per fused multiply-add instead of two, so every row agrees with
+    the oracle within the summation bound 2 k eps sum_k |a_k p_k|.  Matrix
+    values and p come from the oracle side and are uploaded."""
     xi = inputs.draws(M, N, seed=21)
     c = Case(h, kind, n, N, aniso, S, xi)
     rng = np.random.default_rng(22)
@@ -254,7 +255,9 @@ def test_spmv_bit_exact_and_lane_dots(h, kind, n, N, aniso, S, M):
     work = torch.empty(ens.ens_pcg_workspace_size(c.J, c.nnz, S, c.E), dtype=torch.uint8, device="cuda")
     ens.ens_spmv(h, c.J, c.nnz, S, c.E, c.rowptr, c.colidx, vals, p, q, pq, work)
     Q = c.lane_vec(q)
+    eps = np.finfo(np.float64).eps
     for L in range(c.E * S):
         ref = O.spmv(rp, ci, V[L], P[L])
-        assert np.array_equal(Q[L], ref)
+        mag = O.spmv(rp, ci, np.abs(V[L]), np.abs(P[L]))
+        assert np.all(np.abs(Q[L] - ref) <= 2 * 9 * eps * mag)
         assert pq[L].item() == pytest.approx(float(P[L] @ ref), rel=1e-12)

@@ -68,17 +68,21 @@ struct Args {
     cudaGraphConditionalHandle cond;
 };
 
+// Rows per block: at least 256 (so the per-block reduction tail is amortised
+// over enough rows) and enough to give about four blocks per SM for one
+// ensemble; a multiple of 256, so every kernel's row pass divides it.  The
+// geometry depends on J only, so a lane's reduction order is the same for any
+// E and any lane position.
 Geo geometry(int J, int S)
 {
-    const int V = S >= 2 ? 2 : 1;
-    const int TPR = S / V;
-    const int RPP = kBlock / TPR;                   // rows per block pass
-    const long long target = 152LL * 8;             // blocks per ensemble when E = 1
-    long long passes = ((long long)J + RPP * target - 1) / (RPP * target);
-    if (passes < 1) passes = 1;
+    (void)S;
+    const long long target = 152LL * 4;
+    long long RT = ((long long)J + target - 1) / target;
+    if (RT < 256) RT = 256;
+    RT = (RT + 255) / 256 * 256;
     Geo g;
-    g.RT = (int)(RPP * passes);
-    g.nblk = (int)((J + g.RT - 1) / g.RT);
+    g.RT = (int)RT;
+    g.nblk = (int)((J + RT - 1) / RT);
     return g;
 }
 
@@ -141,21 +145,28 @@ template <> struct Vec<2> {
     }
 };
 
-template <int S> struct LaneGeo {
-    static constexpr int V = S >= 2 ? 2 : 1;
+// V lanes per thread.  The vector kernels (K0, K3, K4) take two lanes per
+// thread as one 16-byte access; the SpMV (K2) takes one lane per thread, which
+// halves its registers and doubles its resident warps -- it is bound by the
+// FP64 issue rate, and more independent multiply-add chains per SM keep that
+// pipe busier (two lanes per thread are kept only for S = 64, so a row stays
+// within one warp).
+template <int S, int V_> struct LaneGeo {
+    static constexpr int V = V_;
     static constexpr int TPR = S / V;          // threads per row
     static constexpr int RPP = kBlock / TPR;   // rows per block pass
     static constexpr int G = kBlock / S;       // groups in the final cross-block sum
 };
+template <int S> using VecGeo = LaneGeo<S, (S >= 2 ? 2 : 1)>;
+template <int S> using SpmvGeo = LaneGeo<S, (S >= 64 ? 2 : 1)>;
 
 // Per-lane block reduction of NS sums, then the cross-block sum in the last
 // block of the ensemble.  Returns true in that block, with tot[ns * S + s]
 // holding the totals (shared memory).
-template <int S, int NS>
-__device__ bool reduce_lanes(double (&acc)[NS][LaneGeo<S>::V], double *part_base[NS], int e, int nblk,
+template <class LG, int S, int NS>
+__device__ bool reduce_lanes(double (&acc)[NS][LG::V], double *part_base[NS], int e, int nblk,
                              int *counter, double *tot)
 {
-    using LG = LaneGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR;
     __shared__ double warp_part[kBlock / 32][NS][S];
     __shared__ double grp[LG::G][NS][S];
@@ -182,9 +193,13 @@ __device__ bool reduce_lanes(double (&acc)[NS][LaneGeo<S>::V], double *part_base
             part_base[ns][((size_t)e * nblk + blockIdx.x) * S + tid] = s;
         }
     }
-    __threadfence();
+    // The barrier orders the partial writes before thread 0's fence, and the
+    // fence is cumulative, so one fence publishes the whole block's partials.
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(counter, 1) == nblk - 1);
+    if (tid == 0) {
+        __threadfence();
+        s_last = (atomicAdd(counter, 1) == nblk - 1);
+    }
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
@@ -226,7 +241,7 @@ __device__ __forceinline__ void freeze(const Args &a, int L, int st, int iters, 
 template <int S>
 __global__ void __launch_bounds__(kBlock) k_init(Args a)
 {
-    using LG = LaneGeo<S>;
+    using LG = VecGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
     const int e = blockIdx.y;
     const int lane0 = (threadIdx.x % TPR) * V;
@@ -253,7 +268,7 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a)
     __shared__ int dead;
     if (threadIdx.x == 0) dead = 0;
     double *parts[2] = {a.w.part0, a.w.part1};
-    if (!reduce_lanes<S, 2>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_INIT, tot)) return;
+    if (!reduce_lanes<LG, S, 2>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_INIT, tot)) return;
     int *live_cnt = &dead;  // counts live lanes here
     if (threadIdx.x < S) {
         const int s = threadIdx.x, L = e * S + s;
@@ -292,9 +307,9 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a)
 constexpr int kChunk = 9;  // nonzeros loaded together per row (covers the 5/7/9-point rows)
 
 template <int S>
-__global__ void __launch_bounds__(kBlock) k_spmv(Args a)
+__global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4))) k_spmv(Args a)
 {
-    using LG = LaneGeo<S>;
+    using LG = SpmvGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
     const int e = blockIdx.y;
     if (a.w.ens_live[e] == 0) return;
@@ -345,7 +360,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv(Args a)
     __shared__ int dead;
     if (threadIdx.x == 0) dead = 0;
     double *parts[1] = {a.w.part0};
-    if (!reduce_lanes<S, 1>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_SPMV, tot)) return;
+    if (!reduce_lanes<LG, S, 1>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_SPMV, tot)) return;
     if (threadIdx.x < S && a.pq_out) {
         a.pq_out[e * S + threadIdx.x] = tot[threadIdx.x];
     } else if (threadIdx.x < S) {
@@ -371,7 +386,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv(Args a)
 template <int S>
 __global__ void __launch_bounds__(kBlock) k_update(Args a)
 {
-    using LG = LaneGeo<S>;
+    using LG = VecGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
     const int e = blockIdx.y;
     if (a.w.ens_live[e] == 0) return;
@@ -414,7 +429,7 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a)
     __shared__ int dead;
     if (threadIdx.x == 0) dead = 0;
     double *parts[2] = {a.w.part0, a.w.part1};
-    if (!reduce_lanes<S, 2>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_UPD, tot)) return;
+    if (!reduce_lanes<LG, S, 2>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_UPD, tot)) return;
     if (threadIdx.x < S) {
         const int L = e * S + threadIdx.x;
         if (a.w.live[L]) {
@@ -445,7 +460,7 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a)
 template <int S>
 __global__ void __launch_bounds__(kBlock) k_direction(Args a)
 {
-    using LG = LaneGeo<S>;
+    using LG = VecGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
     const int e = blockIdx.y;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {

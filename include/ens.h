@@ -130,6 +130,33 @@ int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   double rtol, int maxit, int32_t *iters, double *relres, int32_t *status,
                   void *work, size_t work_bytes, void *stream);
 
+/* The same solve for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this exists for code that must not call cudaMalloc --
+ * for example code running under an allocator that owns all device memory, or
+ * a plug-in that may not create or grow device allocations -- and so cannot
+ * provide the `work` buffer of ens_pcg_solve.  Its scratch is a file-scope
+ * device array of ENS_PCG_STATIC_SCRATCH_BYTES (8 MiB), which every GPU that
+ * loads the library holds until the process exits; a problem whose workspace
+ * (ens_pcg_workspace_size) exceeds it is rejected with ENS_EINVAL and a message.
+ * The caller still provides every input and output, as for ens_pcg_solve.
+ *   - It runs on the calling thread's current device.  Its first call on a
+ *     device looks up the array's device address there (once per device);
+ *     make that first call before any stream capture.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine, and
+ *     instantiates no CUDA graph: the iteration is launched from the host,
+ *     which reads the live-lane count back every 16 trips (so the call
+ *     synchronises `stream`).
+ *   - Every call shares the one array: calls that overlap on the GPU (other
+ *     streams, other threads) race and must not be issued; the array keeps the
+ *     previous call's contents, and the call clears what must start at zero.
+ *   - h may be NULL (then no message is kept). */
+#define ENS_PCG_STATIC_SCRATCH_BYTES ((size_t)8 << 20)
+int ens_pcg_solve_static(ens_handle h, int J, int64_t nnz, int S, int E,
+                         const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                         const double *dinv, const double *b, double *x, const uint8_t *active,
+                         double rtol, int maxit, int32_t *iters, double *relres, int32_t *status,
+                         void *stream);
+
 /* Ensemble SpMV (Section 2.3: the matrix-vector product of the commuted
  * Kronecker system, each nonzero's S values applied to the S lanes of its
  * column): q[E][J][S] = A_s p_s for every lane, and pq[E][S] = p_s^T q_s

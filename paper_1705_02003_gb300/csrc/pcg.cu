@@ -28,6 +28,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 namespace ens {
 
@@ -724,6 +725,87 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
     }
     k_finish<<<(E * S + 255) / 256, 256, 0, st>>>(a);
     ENS_LAUNCH_CHECK(h, "ens_pcg_solve: finish kernel");
+    return ENS_OK;
+}
+
+// ---- the solve for callers that cannot allocate device memory ------------------
+// Some callers cannot call cudaMalloc at all: code running under an allocator
+// that owns all device memory, or plug-ins that may not create or grow device
+// allocations.  For them ens_pcg_solve_static takes its scratch from this
+// file-scope array instead of a caller workspace.  It is small on purpose, as
+// every GPU that loads the library holds it until the process exits.
+constexpr size_t kStaticScratchBytes = ENS_PCG_STATIC_SCRATCH_BYTES;  // 8 MiB
+static __device__ __align__(256) unsigned char g_pcg_scratch[kStaticScratchBytes];
+
+namespace ens {
+namespace {
+std::mutex g_scratch_mu;
+void *g_scratch_addr[128] = {};  // device address of g_pcg_scratch, per device
+
+// The symbol's name is a host-side stand-in; the device address is looked up
+// once per device, with that device current.
+int scratch_address(ens_ctx *h, void **out)
+{
+    int dev = 0;
+    ENS_CUDA_CHECK(h, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        ENS_CUDA_CHECK(h, cudaGetSymbolAddress(&p, g_pcg_scratch));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return ENS_OK;
+}
+}  // namespace
+}  // namespace ens
+
+extern "C" int ens_pcg_solve_static(ens_handle h, int J, int64_t nnz, int S, int E, const int32_t *rowptr,
+                                    const int32_t *colidx, const double *vals, const double *dinv,
+                                    const double *b, double *x, const uint8_t *active, double rtol, int maxit,
+                                    int32_t *iters, double *relres, int32_t *status, void *stream)
+{
+    if (!lane_count_ok(S)) return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: S must be 1,2,4,...,64");
+    if (J <= 0 || nnz <= 0 || E < 0 || nnz >= (1LL << 31))
+        return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: bad J / nnz / E");
+    if (E == 0) return ENS_OK;
+    if (!(rtol >= 0.0) || maxit < 0) return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: bad rtol / maxit");
+    if (!rowptr || !colidx || !vals || !dinv || !b || !x || !iters || !relres || !status)
+        return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: null pointer");
+    if (((uintptr_t)vals | (uintptr_t)dinv | (uintptr_t)b | (uintptr_t)x) & 15)
+        return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: arrays must be 16-byte aligned");
+    Geo g = geometry(J, S);
+    const size_t need = layout(J, S, E, g, nullptr, nullptr);
+    if (need > kStaticScratchBytes)
+        return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: this problem needs " + std::to_string(need) +
+                                            " bytes of scratch; the static scratch holds " +
+                                            std::to_string(kStaticScratchBytes) + " (use ens_pcg_solve)");
+    void *scratch = nullptr;
+    int rc = scratch_address(h, &scratch);
+    if (rc) return rc;
+    Args a;
+    memset(&a, 0, sizeof(a));
+    a.J = J; a.S = S; a.E = E; a.maxit = maxit; a.nnz = nnz; a.rtol = rtol; a.g = g;
+    a.rowptr = rowptr; a.colidx = colidx; a.vals = vals; a.dinv = dinv; a.b = b; a.x = x;
+    a.active = active; a.iters = iters; a.status = status; a.relres = relres;
+    layout(J, S, E, g, &a.w, (char *)scratch);
+    cudaStream_t st = (cudaStream_t)stream;
+    // The array keeps the previous call's contents: the counters and the loop
+    // control start from zero here; everything else is written before it is read.
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl, 0, CTL_WORDS * sizeof(int), st));
+    dispatch_init(a, st);
+    ENS_LAUNCH_CHECK(h, "ens_pcg_solve_static: init kernel");
+    int ctl[2] = {1, 0};
+    while (ctl[0] > 0 && ctl[1] < maxit) {
+        for (int t = 0; t < 16; t++) dispatch_body(a, st);
+        ENS_LAUNCH_CHECK(h, "ens_pcg_solve_static: loop kernels");
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(ctl, a.w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+        ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+    }
+    k_finish<<<(E * S + 255) / 256, 256, 0, st>>>(a);
+    ENS_LAUNCH_CHECK(h, "ens_pcg_solve_static: finish kernel");
     return ENS_OK;
 }
 

@@ -23,7 +23,8 @@ LANE_CONVERGED, LANE_MAXIT, LANE_BREAKDOWN, LANE_BADINPUT, LANE_INACTIVE = 0, 1,
 
 EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "ens_pattern",
            "ens_assemble", "ens_pcg_workspace_size", "ens_pcg_solve", "ens_group", "ens_sort_chunk",
-           "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv")
+           "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv",
+           "ens_pcg_solve_static")
 
 _lib = None
 _lock = threading.Lock()
@@ -76,6 +77,8 @@ def _declare(L):
     L.ens_sg_eval.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_int, vp, vp, vp, vp]
     L.ens_qoi.argtypes = [vp, c.c_int, c.c_int, c.c_int, vp, vp, vp, vp]
     L.ens_spmv.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_pcg_solve_static.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp,
+                                       c.c_double, c.c_int, vp, vp, vp, vp]
     i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -218,6 +221,30 @@ def ens_spmv(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx, vals, 
     rc = load().ens_spmv(h.ptr, int(J), int(nnz), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
                          _ptr(p), _ptr(q), _ptr(pq), _ptr(work), work.numel(), _stream(stream))
     h.check(rc, "ens_spmv")
+
+
+STATIC_SCRATCH_BYTES = 8 << 20
+
+
+def ens_pcg_solve_static(h, J: int, nnz: int, S: int, E: int, rowptr, colidx, vals, dinv, b, x, active,
+                         rtol: float, maxit: int, iters, relres, status, stream=None):
+    """ens_pcg_solve without a caller workspace: for callers that may not
+    allocate device memory; scratch is the library's fixed 8 MiB device array.
+    h may be None."""
+    for t, nm, dt in ((vals, "vals", torch.float64), (dinv, "dinv", torch.float64), (b, "b", torch.float64),
+                      (x, "x", torch.float64), (iters, "iters", torch.int32), (relres, "relres", torch.float64),
+                      (status, "status", torch.int32)):
+        _check_dtype(t, dt, nm)
+    if vals.numel() != E * nnz * S or x.numel() != E * J * S or iters.numel() != E * S:
+        raise ValueError("array sizes do not match E, J, nnz, S")
+    rc = load().ens_pcg_solve_static(h.ptr if h is not None else None, int(J), int(nnz), int(S), int(E),
+                                     _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(dinv), _ptr(b), _ptr(x),
+                                     _ptr(active), float(rtol), int(maxit), _ptr(iters), _ptr(relres),
+                                     _ptr(status), _stream(stream))
+    if h is not None:
+        h.check(rc, "ens_pcg_solve_static")
+    elif rc != OK:
+        raise EnsError(f"ens_pcg_solve_static failed ({rc})")
 
 
 def ens_group(h: Handle, lvl, idx, surplus, yq, S: int, pred, perm, stream=None) -> int:

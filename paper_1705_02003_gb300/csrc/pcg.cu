@@ -123,6 +123,7 @@ template <int V> struct Vec;
 template <> struct Vec<1> {
     double v[1];
     __device__ __forceinline__ void load(const double *p) { v[0] = *p; }
+    __device__ __forceinline__ void load_ro(const double *p) { v[0] = __ldg(p); }
     __device__ __forceinline__ void load_stream(const double *p) { v[0] = __ldcs(p); }
     __device__ __forceinline__ void store(double *p) const { *p = v[0]; }
 };
@@ -137,6 +138,12 @@ template <> struct Vec<2> {
     __device__ __forceinline__ void load_stream(const double *p)
     {
         double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+    __device__ __forceinline__ void load_ro(const double *p)
+    {
+        double2 t = __ldg(reinterpret_cast<const double2 *>(p));
         v[0] = t.x;
         v[1] = t.y;
     }
@@ -239,8 +246,13 @@ __device__ __forceinline__ void freeze(const Args &a, int L, int st, int iters, 
 }
 
 // ---- K0: x = 0, r = b, p = D^-1 b; b^T b and r^T D^-1 r per lane ------------
+// Streamed arrays are passed as kernel parameters: read out of the by-value
+// Args struct instead, their loads were measured to lose half of the kernel's
+// memory-level parallelism on sm_103a.
 template <int S>
-__global__ void __launch_bounds__(kBlock) k_init(Args a)
+__global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restrict__ bb, const double *__restrict__ dinv,
+                                                 double *__restrict__ xx, double *__restrict__ rr,
+                                                 double *__restrict__ pp)
 {
     using LG = VecGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
@@ -252,8 +264,8 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a)
     for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
         size_t o = vbase + (size_t)r * S + lane0;
         Vec<V> bv, dv, xv, pv;
-        bv.load(a.b + o);
-        dv.load(a.dinv + o);
+        bv.load_ro(bb + o);
+        dv.load_ro(dinv + o);
 #pragma unroll
         for (int v = 0; v < V; v++) {
             xv.v[v] = 0.0;
@@ -261,9 +273,9 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a)
             acc[0][v] = fma(bv.v[v], bv.v[v], acc[0][v]);
             acc[1][v] = fma(bv.v[v], pv.v[v], acc[1][v]);
         }
-        xv.store(a.x + o);
-        bv.store(a.w.r + o);
-        pv.store(a.w.p + o);
+        xv.store(xx + o);
+        bv.store(rr + o);
+        pv.store(pp + o);
     }
     __shared__ double tot[2 * S];
     __shared__ int dead;
@@ -308,7 +320,9 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a)
 constexpr int kChunk = 9;  // nonzeros loaded together per row (covers the 5/7/9-point rows)
 
 template <int S>
-__global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4))) k_spmv(Args a)
+__global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4)))
+    k_spmv(Args a, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+           const double *__restrict__ vals_all, const double *__restrict__ p_all, double *__restrict__ q_all)
 {
     using LG = SpmvGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
@@ -320,12 +334,12 @@ __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4))) k_sp
     if (V == 2) mine = mine || a.w.live[L0 + 1] != 0;
     double acc[1][V] = {};
     if (mine) {
-        const double *vals = a.vals + (size_t)e * a.nnz * S + lane0;
-        const double *p = a.w.p + (size_t)e * a.J * S + lane0;
-        double *q = a.w.q + (size_t)e * a.J * S + lane0;
+        const double *__restrict__ vals = vals_all + (size_t)e * a.nnz * S + lane0;
+        const double *__restrict__ p = p_all + (size_t)e * a.J * S + lane0;
+        double *__restrict__ q = q_all + (size_t)e * a.J * S + lane0;
         const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
         for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
-            const int k0 = __ldg(a.rowptr + r), k1 = __ldg(a.rowptr + r + 1);
+            const int k0 = __ldg(rowptr + r), k1 = __ldg(rowptr + r + 1);
             double s[V];
 #pragma unroll
             for (int v = 0; v < V; v++) s[v] = 0.0;
@@ -334,12 +348,12 @@ __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4))) k_sp
                 Vec<V> av[kChunk], xv[kChunk];
 #pragma unroll
                 for (int u = 0; u < kChunk; u++)
-                    if (kb + u < k1) c[u] = __ldg(a.colidx + kb + u);
+                    if (kb + u < k1) c[u] = __ldg(colidx + kb + u);
 #pragma unroll
                 for (int u = 0; u < kChunk; u++)
                     if (kb + u < k1) {
                         av[u].load_stream(vals + (size_t)(kb + u) * S);
-                        xv[u].load(p + (size_t)c[u] * S);
+                        xv[u].load_ro(p + (size_t)c[u] * S);
                     }
 #pragma unroll
                 for (int u = 0; u < kChunk; u++)
@@ -352,7 +366,7 @@ __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4))) k_sp
 #pragma unroll
             for (int v = 0; v < V; v++) qv.v[v] = s[v];
             qv.store(q + (size_t)r * S);
-            pr.load(p + (size_t)r * S);
+            pr.load_ro(p + (size_t)r * S);
 #pragma unroll
             for (int v = 0; v < V; v++) acc[0][v] = fma(pr.v[v], s[v], acc[0][v]);
         }
@@ -385,7 +399,9 @@ __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4))) k_sp
 
 // ---- K3: x += alpha p, r -= alpha q; r^T r and r^T D^-1 r -> convergence, beta ----
 template <int S>
-__global__ void __launch_bounds__(kBlock) k_update(Args a)
+__global__ void __launch_bounds__(kBlock) k_update(Args a, double *__restrict__ xx, double *__restrict__ rr,
+                                                   const double *__restrict__ pp, const double *__restrict__ qq,
+                                                   const double *__restrict__ dinv)
 {
     using LG = VecGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
@@ -409,11 +425,11 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a)
         for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
             const size_t o = vb + (size_t)r * S;
             Vec<V> xv, rv, pv, qv, dv;
-            xv.load(a.x + o);
-            rv.load(a.w.r + o);
-            pv.load(a.w.p + o);
-            qv.load(a.w.q + o);
-            dv.load(a.dinv + o);
+            xv.load(xx + o);
+            rv.load(rr + o);
+            pv.load_ro(pp + o);
+            qv.load_ro(qq + o);
+            dv.load_ro(dinv + o);
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 if (!lv[v]) continue;  // frozen lane: keep x and r
@@ -422,8 +438,8 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a)
                 acc[0][v] = fma(rv.v[v], rv.v[v], acc[0][v]);
                 acc[1][v] = fma(rv.v[v], dv.v[v] * rv.v[v], acc[1][v]);
             }
-            xv.store(a.x + o);
-            rv.store(a.w.r + o);
+            xv.store(xx + o);
+            rv.store(rr + o);
         }
     }
     __shared__ double tot[2 * S];
@@ -459,7 +475,8 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a)
 
 // ---- K4: p = D^-1 r + beta p; loop control -------------------------------------
 template <int S>
-__global__ void __launch_bounds__(kBlock) k_direction(Args a)
+__global__ void __launch_bounds__(kBlock) k_direction(Args a, const double *__restrict__ rr,
+                                                      const double *__restrict__ dinv, double *__restrict__ pp)
 {
     using LG = VecGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
@@ -489,13 +506,13 @@ __global__ void __launch_bounds__(kBlock) k_direction(Args a)
     for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
         const size_t o = vb + (size_t)r * S;
         Vec<V> rv, dv, pv;
-        rv.load(a.w.r + o);
-        dv.load(a.dinv + o);
-        pv.load(a.w.p + o);
+        rv.load_ro(rr + o);
+        dv.load_ro(dinv + o);
+        pv.load(pp + o);
 #pragma unroll
         for (int v = 0; v < V; v++)
             if (lv[v]) pv.v[v] = fma(be[v], pv.v[v], dv.v[v] * rv.v[v]);
-        pv.store(a.w.p + o);
+        pv.store(pp + o);
     }
 }
 
@@ -524,7 +541,7 @@ template <int S>
 void launch_spmv(const Args &a, cudaStream_t st)
 {
     dim3 grid(a.g.nblk, a.E);
-    k_spmv<S><<<grid, kBlock, 0, st>>>(a);
+    k_spmv<S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, a.vals, a.w.p, a.w.q);
 }
 
 void dispatch_spmv(const Args &a, cudaStream_t st)
@@ -544,16 +561,16 @@ template <int S>
 void launch_body(const Args &a, cudaStream_t st)
 {
     dim3 grid(a.g.nblk, a.E);
-    k_spmv<S><<<grid, kBlock, 0, st>>>(a);
-    k_update<S><<<grid, kBlock, 0, st>>>(a);
-    k_direction<S><<<grid, kBlock, 0, st>>>(a);
+    k_spmv<S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, a.vals, a.w.p, a.w.q);
+    k_update<S><<<grid, kBlock, 0, st>>>(a, a.x, a.w.r, a.w.p, a.w.q, a.dinv);
+    k_direction<S><<<grid, kBlock, 0, st>>>(a, a.w.r, a.dinv, a.w.p);
 }
 
 template <int S>
 void launch_init(const Args &a, cudaStream_t st)
 {
     dim3 grid(a.g.nblk, a.E);
-    k_init<S><<<grid, kBlock, 0, st>>>(a);
+    k_init<S><<<grid, kBlock, 0, st>>>(a, a.b, a.dinv, a.x, a.w.r, a.w.p);
 }
 
 void dispatch_body(const Args &a, cudaStream_t st)

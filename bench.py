@@ -36,6 +36,22 @@ if ROOT not in sys.path:
 METRIC = "sample-solves/s at rel-res 1e-8: ensemble PCG vs per-sample PCG; SpMV HBM GB/s"
 
 
+# FP64 roof of GB300: the FP64 pipe retires two lanes per clock per SM (the
+# pipe-activity counter of K2 gives 1.67 per active cycle at 84 % activity),
+# so 152 SMs x 2 FMA x 2.07 GHz = 630 G FMA/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_SOURCE = "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)"
+
+# DRAM bytes of one K2 launch measured by ncu on the E = 8 case of the same
+# kernel (profiles/k_spmv_q1_256_E8.md), scaled by the units a launch processes.
+SPMV_TRAFFIC_PER_ENSEMBLE = {"q1_256_adaptive": (673.70368e6 + 39.161856e6) / 8}
+
+
+def spmv_traffic(wl, E):
+    t = SPMV_TRAFFIC_PER_ENSEMBLE.get(wl.name)
+    return None if t is None else t * E
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -268,11 +284,26 @@ def run_ours(args, wl):
     torch.cuda.synchronize()
     t_spmv = e0.elapsed_time(e1) / 1e3 / reps
     spmv_bytes = E * (8 * sol.nnz * sol.S + 4 * sol.nnz + 4 * (sol.J + 1) + 16 * sol.J * sol.S)
+    spmv_fma = E * sol.S * (sol.nnz + sol.J)  # one fused multiply-add per nonzero-lane, one per row-lane for p^T q
     peak, peak_kind = peaks()
     achieved = spmv_bytes / t_spmv / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_spmv (K2)", "peak_source": peak_kind,
-                "bytes_per_launch": spmv_bytes, "launch_ms": t_spmv * 1e3}
+    tflops = 2.0 * spmv_fma / t_spmv / 1e12
+    roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": spmv_traffic(wl, E),
+                "kernel": "k_spmv (K2), FP64", "peak_source": FP64_PEAK_SOURCE,
+                "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_source": peak_kind},
+                "bytes_per_launch": spmv_bytes, "fma_per_launch": spmv_fma, "launch_ms": t_spmv * 1e3}
+    # the whole path: every lane of an ensemble streams until the slowest lane stops
+    charged = sum(float(np.max(run["I"][a + perm[k:k + sol.S]]))
+                  for (a, b), perm in zip(run["levels"], run["perms"]) for k in range(0, b - a, sol.S)) * sol.S
+    b_alg = 8 * sol.nnz + 72 * sol.J + (4 * sol.nnz + 4 * (sol.J + 1)) / sol.S
+    fma_it = sol.nnz + 8 * sol.J  # K2: nnz + J, K3: 5 J, K4: 2 J per sample-iteration
+    t_it = max(b_alg / (peak * 1e9), 2.0 * fma_it / (FP64_PEAK_TFLOPS * 1e12))
+    path_roof = M / (charged * t_it)
+    roofline["path"] = {"value": path_roof, "unit": "sample-solves/s", "frac": value / path_roof,
+                        "sample_iterations_charged": charged, "bytes_per_sample_iteration": b_alg,
+                        "fma_per_sample_iteration": fma_it}
 
     # end to end through the public API with host buffers: the loop copies each
     # level's points in and its surpluses out; in addition every solve's

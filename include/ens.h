@@ -130,6 +130,49 @@ int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   double rtol, int maxit, int32_t *iters, double *relres, int32_t *status,
                   void *work, size_t work_bytes, void *stream);
 
+/* Bytes of caller workspace ens_adjoint_grad needs (0 for bad arguments). */
+size_t ens_adjoint_workspace_size(const ens_problem *p, int S, int E);
+
+/* Adjoint gradient of a linear quantity of interest (the differentiation
+ * layer; the paper's QoI G_u of Section 2.1 is such a functional).  With
+ * u[E][J][S] the solutions of A(xi) u = b and lam[E][J][S] those of the adjoint
+ * A(xi) lam = w (A is symmetric; b does not depend on xi), writes
+ *   grad[E][S][nparam] = dQ/dxi = -lam^T (dA/dxi) u,   Q = w^T u,
+ * summed face by face over the FD operator (FD5 and FD7 problems only;
+ * ENS_ENOTSUP for Q1).  xi[E][S][nparam] as for ens_assemble.  Deterministic:
+ * fixed per-lane summation order. */
+int ens_adjoint_grad(ens_handle h, const ens_problem *p, int S, int E, const double *xi,
+                     const double *u, const double *lam, double *grad, void *work,
+                     size_t work_bytes, void *stream);
+
+/* Bytes of caller workspace ens_pcg_solve_ir needs. */
+size_t ens_pcg_ir_workspace_size(int J, int64_t nnz, int S, int E);
+
+/* Mixed precision: FP32 matrix values and inner Jacobi-PCG inside FP64
+ * iterative refinement (the precision layer; the paper solves in FP64
+ * throughout, Section 4).  Per lane: x = 0; then repeatedly
+ *   r = b - A x with the FP64 values `vals` (FP64 residual and norm);
+ *   stop when ||r||_2 <= rtol ||b||_2 (status CONVERGED), or after maxit_outer
+ *   corrections (MAXIT);
+ *   solve A32 d = r with the FP32 values `vals32` (ens_assemble with
+ *   vals_f32 = 1) by the same ensemble Jacobi-PCG, FP32 vectors but FP64 inner
+ *   products, norms and CG scalars, to ||r - A32 d|| <= rtol_inner ||r|| or
+ *   maxit_inner iterations;
+ *   x = x + d in FP64.
+ * A lane whose inner solve cannot make progress (breakdown before its first
+ * update, or a non-finite residual) stops with status BREAKDOWN.
+ * Outputs: x[E][J][S], iters[E][S] = inner iterations summed over the
+ * corrections, outer_its[E][S] = corrections applied, relres[E][S] = the FP64
+ * relative residual ||b - A x|| / ||b|| of the returned x, status[E][S].
+ * The host reads the live-lane count back once per correction, so the call
+ * synchronises `stream`. */
+int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E,
+                     const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                     const float *vals32, const double *dinv, const double *b, double *x,
+                     const uint8_t *active, double rtol, double rtol_inner, int maxit_inner,
+                     int maxit_outer, int32_t *iters, int32_t *outer_its, double *relres,
+                     int32_t *status, void *work, size_t work_bytes, void *stream);
+
 /* The same solve for callers that cannot allocate device memory.  The paper
  * has no counterpart: this exists for code that must not call cudaMalloc --
  * for example code running under an allocator that owns all device memory, or

@@ -1,4 +1,5 @@
-// pcg.cu -- ensemble Jacobi-PCG with per-sample inner products (K2, K3, K4).
+// pcg.cu -- ensemble Jacobi-PCG with per-sample inner products (K2, K3, K4),
+// its FP32-in-FP64 iterative-refinement form, and the stand-alone SpMV.
 //
 // Section 2.3: the S samples of an ensemble share one graph; their values are
 // interleaved [nnz][S] and their vectors [J][S].  Inner products and norms are
@@ -12,10 +13,13 @@
 // One CG iteration is three kernels, each followed by a per-lane reduction
 // finished by the last block of the ensemble to arrive (fixed block order, so
 // results are deterministic and independent of E and of the other lanes):
-//   K2  q = A p (CSR, one column index per nonzero for all S lanes, the S
-//       values as 16-byte vector loads), partial p^T q       -> alpha
-//   K3  x += alpha p, r -= alpha q, partial r^T r, r^T D^-1 r  -> convergence, beta
+//   K2  q = A p (CSR, one column index per nonzero for all S lanes), p^T q  -> alpha
+//   K3  x += alpha p, r -= alpha q, r^T r, r^T D^-1 r                       -> convergence, beta
 //   K4  p = D^-1 r + beta p; block (0,0) also drives the graph's while loop.
+// The kernels are templates over the value type T of the matrix and vectors:
+// T = double is the FP64 method; T = float is the inner solve of the
+// mixed-precision form, whose inner products, norms and CG scalars stay FP64.
+//
 // Arithmetic: GB300 issues about two FP64 operations per clock per SM, which
 // is the binding limit of these kernels before HBM is, so every
 // multiply-accumulate is one fused multiply-add (the per-row sums keep the
@@ -34,11 +38,11 @@ namespace ens {
 
 namespace {
 
-enum { CTL_NLIVE = 0, CTL_TRIPS = 1, CTL_WORDS = 16 };
-enum { CNT_INIT = 0, CNT_SPMV = 1, CNT_UPD = 2, CNT_KINDS = 4 };
+enum { CTL_NLIVE = 0, CTL_TRIPS = 1, CTL_OUTER_LIVE = 2, CTL_WORDS = 16 };
+enum { CNT_INIT = 0, CNT_SPMV = 1, CNT_UPD = 2, CNT_RES = 3, CNT_KINDS = 4 };
 
 struct Ws {
-    double *r, *p, *q;      // [E][J][S]
+    void *r, *p, *q;        // [E][J][S] of the loop's value type
     double *part0, *part1;  // [E][nblk][S]
     double *bnorm, *rz, *alpha, *beta, *rr;  // [E][S]
     int *k, *live;          // [E][S]
@@ -58,8 +62,9 @@ struct Args {
     double rtol;
     Geo g;
     const int32_t *rowptr, *colidx;
-    const double *vals, *dinv, *b;
-    double *x;
+    const void *vals, *dinv;  // value type of the loop
+    const double *b;          // right-hand side (FP64 in both forms)
+    void *x;                  // value type of the loop
     const uint8_t *active;
     int32_t *iters, *status;
     double *relres;
@@ -87,86 +92,105 @@ Geo geometry(int J, int S)
     return g;
 }
 
-size_t layout(int J, int S, int E, const Geo &g, Ws *w, char *base)
-{
+struct Bump {
     size_t off = 0;
-    auto take = [&](size_t bytes) {
+    char *base;
+    explicit Bump(char *b) : base(b) {}
+    void *take(size_t bytes)
+    {
         size_t o = off;
         off = align256(off + bytes);
         return base ? (void *)(base + o) : nullptr;
-    };
-    size_t vec = (size_t)E * J * S * sizeof(double);
+    }
+};
+
+void lay_loop(Bump &m, int J, int S, int E, const Geo &g, size_t tsize, Ws *w)
+{
+    size_t vec = (size_t)E * J * S * tsize;
     size_t part = (size_t)E * g.nblk * S * sizeof(double);
     size_t lane = (size_t)E * S;
-    Ws t;
-    t.r = (double *)take(vec);
-    t.p = (double *)take(vec);
-    t.q = (double *)take(vec);
-    t.part0 = (double *)take(part);
-    t.part1 = (double *)take(part);
-    t.bnorm = (double *)take(lane * 8);
-    t.rz = (double *)take(lane * 8);
-    t.alpha = (double *)take(lane * 8);
-    t.beta = (double *)take(lane * 8);
-    t.rr = (double *)take(lane * 8);
-    t.k = (int *)take(lane * 4);
-    t.live = (int *)take(lane * 4);
-    t.ens_live = (int *)take((size_t)E * 4);
-    t.counter = (int *)take((size_t)E * CNT_KINDS * 4);
-    t.ctl = (int *)take(CTL_WORDS * 4);
-    if (w) *w = t;
-    return off;
+    w->r = m.take(vec);
+    w->p = m.take(vec);
+    w->q = m.take(vec);
+    w->part0 = (double *)m.take(part);
+    w->part1 = (double *)m.take(part);
+    w->bnorm = (double *)m.take(lane * 8);
+    w->rz = (double *)m.take(lane * 8);
+    w->alpha = (double *)m.take(lane * 8);
+    w->beta = (double *)m.take(lane * 8);
+    w->rr = (double *)m.take(lane * 8);
+    w->k = (int *)m.take(lane * 4);
+    w->live = (int *)m.take(lane * 4);
+    w->ens_live = (int *)m.take((size_t)E * 4);
+    w->counter = (int *)m.take((size_t)E * CNT_KINDS * 4);
+    w->ctl = (int *)m.take(CTL_WORDS * 4);
 }
 
-// ---- lane vectors: V = 2 consecutive lanes per thread as one 16-byte access --
-template <int V> struct Vec;
-template <> struct Vec<1> {
-    double v[1];
-    __device__ __forceinline__ void load(const double *p) { v[0] = *p; }
-    __device__ __forceinline__ void load_ro(const double *p) { v[0] = __ldg(p); }
-    __device__ __forceinline__ void load_stream(const double *p) { v[0] = __ldcs(p); }
-    __device__ __forceinline__ void store(double *p) const { *p = v[0]; }
+size_t layout(int J, int S, int E, const Geo &g, Ws *w, char *base)
+{
+    Bump m(base);
+    Ws t;
+    lay_loop(m, J, S, E, g, sizeof(double), &t);
+    if (w) *w = t;
+    return m.off;
+}
+
+// ---- lane vectors: V consecutive lanes per thread as one access --------------
+template <typename T, int V> struct VT;
+template <> struct VT<double, 1> {
+    using R = double;
+    __device__ __forceinline__ static void get(double *v, R t) { v[0] = t; }
+    __device__ __forceinline__ static R put(const double *v) { return v[0]; }
 };
-template <> struct Vec<2> {
-    double v[2];
-    __device__ __forceinline__ void load(const double *p)
-    {
-        double2 t = *reinterpret_cast<const double2 *>(p);
-        v[0] = t.x;
-        v[1] = t.y;
-    }
-    __device__ __forceinline__ void load_stream(const double *p)
-    {
-        double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
-        v[0] = t.x;
-        v[1] = t.y;
-    }
-    __device__ __forceinline__ void load_ro(const double *p)
-    {
-        double2 t = __ldg(reinterpret_cast<const double2 *>(p));
-        v[0] = t.x;
-        v[1] = t.y;
-    }
-    __device__ __forceinline__ void store(double *p) const
-    {
-        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
-    }
+template <> struct VT<double, 2> {
+    using R = double2;
+    __device__ __forceinline__ static void get(double *v, R t) { v[0] = t.x; v[1] = t.y; }
+    __device__ __forceinline__ static R put(const double *v) { return make_double2(v[0], v[1]); }
+};
+template <> struct VT<float, 1> {
+    using R = float;
+    __device__ __forceinline__ static void get(float *v, R t) { v[0] = t; }
+    __device__ __forceinline__ static R put(const float *v) { return v[0]; }
+};
+template <> struct VT<float, 2> {
+    using R = float2;
+    __device__ __forceinline__ static void get(float *v, R t) { v[0] = t.x; v[1] = t.y; }
+    __device__ __forceinline__ static R put(const float *v) { return make_float2(v[0], v[1]); }
+};
+template <> struct VT<float, 4> {
+    using R = float4;
+    __device__ __forceinline__ static void get(float *v, R t) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    __device__ __forceinline__ static R put(const float *v) { return make_float4(v[0], v[1], v[2], v[3]); }
 };
 
-// V lanes per thread.  The vector kernels (K0, K3, K4) take two lanes per
-// thread as one 16-byte access; the SpMV (K2) takes one lane per thread, which
-// halves its registers and doubles its resident warps -- it is bound by the
-// FP64 issue rate, and more independent multiply-add chains per SM keep that
-// pipe busier (two lanes per thread are kept only for S = 64, so a row stays
-// within one warp).
+template <typename T, int V> struct Vec {
+    using W = VT<T, V>;
+    using R = typename W::R;
+    T v[V];
+    __device__ __forceinline__ void load(const T *p) { W::get(v, *reinterpret_cast<const R *>(p)); }
+    __device__ __forceinline__ void load_ro(const T *p) { W::get(v, __ldg(reinterpret_cast<const R *>(p))); }
+    __device__ __forceinline__ void load_stream(const T *p) { W::get(v, __ldcs(reinterpret_cast<const R *>(p))); }
+    __device__ __forceinline__ void store(T *p) const { *reinterpret_cast<R *>(p) = W::put(v); }
+};
+
+// V lanes per thread.  The vector kernels (K0, K3, K4) move 16 bytes per
+// access (two FP64 or four FP32 lanes); the SpMV (K2) takes one lane per
+// thread, which halves its registers and doubles its resident warps -- in FP64
+// it is bound by the FP64 issue rate, and more independent multiply-add
+// chains per SM keep that pipe busier (two lanes per thread are kept only for
+// S = 64, so a row stays within one warp).
 template <int S, int V_> struct LaneGeo {
     static constexpr int V = V_;
     static constexpr int TPR = S / V;          // threads per row
     static constexpr int RPP = kBlock / TPR;   // rows per block pass
     static constexpr int G = kBlock / S;       // groups in the final cross-block sum
 };
-template <int S> using VecGeo = LaneGeo<S, (S >= 2 ? 2 : 1)>;
+template <typename T, int S>
+using VecGeo = LaneGeo<S, (S >= (int)(16 / sizeof(T)) ? (int)(16 / sizeof(T)) : S)>;
 template <int S> using SpmvGeo = LaneGeo<S, (S >= 64 ? 2 : 1)>;
+
+__device__ __forceinline__ double wide(double v) { return v; }
+__device__ __forceinline__ double wide(float v) { return (double)v; }
 
 // Per-lane block reduction of NS sums, then the cross-block sum in the last
 // block of the ensemble.  Returns true in that block, with tot[ns * S + s]
@@ -245,16 +269,16 @@ __device__ __forceinline__ void freeze(const Args &a, int L, int st, int iters, 
     atomicAdd(dead, 1);
 }
 
-// ---- K0: x = 0, r = b, p = D^-1 b; b^T b and r^T D^-1 r per lane ------------
 // Streamed arrays are passed as kernel parameters: read out of the by-value
 // Args struct instead, their loads were measured to lose half of the kernel's
 // memory-level parallelism on sm_103a.
-template <int S>
-__global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restrict__ bb, const double *__restrict__ dinv,
-                                                 double *__restrict__ xx, double *__restrict__ rr,
-                                                 double *__restrict__ pp)
+
+// ---- K0: x = 0, r = b, p = D^-1 b; r^T r and r^T D^-1 r per lane ------------
+template <typename T, int S>
+__global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restrict__ bb, const T *__restrict__ dinv,
+                                                 T *__restrict__ xx, T *__restrict__ rr, T *__restrict__ pp)
 {
-    using LG = VecGeo<S>;
+    using LG = VecGeo<T, S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
     const int e = blockIdx.y;
     const int lane0 = (threadIdx.x % TPR) * V;
@@ -263,66 +287,65 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restric
     const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
     for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
         size_t o = vbase + (size_t)r * S + lane0;
-        Vec<V> bv, dv, xv, pv;
-        bv.load_ro(bb + o);
+        Vec<T, V> dv, xv, rv, pv;
         dv.load_ro(dinv + o);
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            xv.v[v] = 0.0;
-            pv.v[v] = dv.v[v] * bv.v[v];
-            acc[0][v] = fma(bv.v[v], bv.v[v], acc[0][v]);
-            acc[1][v] = fma(bv.v[v], pv.v[v], acc[1][v]);
+            xv.v[v] = T(0);
+            rv.v[v] = (T)__ldg(bb + o + v);
+            pv.v[v] = dv.v[v] * rv.v[v];
+            acc[0][v] = fma(wide(rv.v[v]), wide(rv.v[v]), acc[0][v]);
+            acc[1][v] = fma(wide(rv.v[v]), wide(pv.v[v]), acc[1][v]);
         }
         xv.store(xx + o);
-        bv.store(rr + o);
+        rv.store(rr + o);
         pv.store(pp + o);
     }
     __shared__ double tot[2 * S];
-    __shared__ int dead;
-    if (threadIdx.x == 0) dead = 0;
+    __shared__ int live_cnt;
+    if (threadIdx.x == 0) live_cnt = 0;
     double *parts[2] = {a.w.part0, a.w.part1};
     if (!reduce_lanes<LG, S, 2>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_INIT, tot)) return;
-    int *live_cnt = &dead;  // counts live lanes here
     if (threadIdx.x < S) {
         const int s = threadIdx.x, L = e * S + s;
-        const double bb = tot[s], rz = tot[S + s];
+        const double bsq = tot[s], rz = tot[S + s];
         const int act = a.active ? (int)a.active[L] : 1;
         a.w.k[L] = 0;
         int live = 0;
         if (!act) {
             a.status[L] = ENS_LANE_INACTIVE; a.iters[L] = 0; a.relres[L] = 0.0;
-        } else if (!isfinite(bb) || !isfinite(rz)) {
+        } else if (!isfinite(bsq) || !isfinite(rz)) {
             a.status[L] = ENS_LANE_BADINPUT; a.iters[L] = 0; a.relres[L] = __longlong_as_double(0x7ff8000000000000LL);
-        } else if (bb == 0.0) {
+        } else if (bsq == 0.0) {
             a.status[L] = ENS_LANE_CONVERGED; a.iters[L] = 0; a.relres[L] = 0.0;
         } else if (a.maxit <= 0) {
             a.status[L] = ENS_LANE_MAXIT; a.iters[L] = 0; a.relres[L] = 1.0;
         } else {
             live = 1;
-            a.w.bnorm[L] = sqrt(bb);
+            a.w.bnorm[L] = sqrt(bsq);
             a.w.rz[L] = rz;
-            a.w.rr[L] = bb;
+            a.w.rr[L] = bsq;
             a.status[L] = ENS_LANE_MAXIT;
             a.iters[L] = 0;
             a.relres[L] = 1.0;
         }
         a.w.live[L] = live;
-        if (live) atomicAdd(live_cnt, 1);
+        if (live) atomicAdd(&live_cnt, 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        a.w.ens_live[e] = *live_cnt;
-        atomicAdd(a.w.ctl + CTL_NLIVE, *live_cnt);
+        a.w.ens_live[e] = live_cnt;
+        atomicAdd(a.w.ctl + CTL_NLIVE, live_cnt);
     }
 }
 
 // ---- K2: q = A p and p^T q per lane -> alpha -----------------------------------
 constexpr int kChunk = 9;  // nonzeros loaded together per row (covers the 5/7/9-point rows)
 
-template <int S>
+template <typename T, int S>
 __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4)))
     k_spmv(Args a, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-           const double *__restrict__ vals_all, const double *__restrict__ p_all, double *__restrict__ q_all)
+           const T *__restrict__ vals_all, const T *__restrict__ p_all, T *__restrict__ q_all)
 {
     using LG = SpmvGeo<S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
@@ -334,18 +357,18 @@ __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4)))
     if (V == 2) mine = mine || a.w.live[L0 + 1] != 0;
     double acc[1][V] = {};
     if (mine) {
-        const double *__restrict__ vals = vals_all + (size_t)e * a.nnz * S + lane0;
-        const double *__restrict__ p = p_all + (size_t)e * a.J * S + lane0;
-        double *__restrict__ q = q_all + (size_t)e * a.J * S + lane0;
+        const T *__restrict__ vals = vals_all + (size_t)e * a.nnz * S + lane0;
+        const T *__restrict__ p = p_all + (size_t)e * a.J * S + lane0;
+        T *__restrict__ q = q_all + (size_t)e * a.J * S + lane0;
         const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
         for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
             const int k0 = __ldg(rowptr + r), k1 = __ldg(rowptr + r + 1);
-            double s[V];
+            T s[V];
 #pragma unroll
-            for (int v = 0; v < V; v++) s[v] = 0.0;
+            for (int v = 0; v < V; v++) s[v] = T(0);
             for (int kb = k0; kb < k1; kb += kChunk) {
                 int c[kChunk];
-                Vec<V> av[kChunk], xv[kChunk];
+                Vec<T, V> av[kChunk], xv[kChunk];
 #pragma unroll
                 for (int u = 0; u < kChunk; u++)
                     if (kb + u < k1) c[u] = __ldg(colidx + kb + u);
@@ -362,13 +385,13 @@ __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4)))
                         for (int v = 0; v < V; v++) s[v] = fma(av[u].v[v], xv[u].v[v], s[v]);
                     }
             }
-            Vec<V> qv, pr;
+            Vec<T, V> qv, pr;
 #pragma unroll
             for (int v = 0; v < V; v++) qv.v[v] = s[v];
             qv.store(q + (size_t)r * S);
             pr.load_ro(p + (size_t)r * S);
 #pragma unroll
-            for (int v = 0; v < V; v++) acc[0][v] = fma(pr.v[v], s[v], acc[0][v]);
+            for (int v = 0; v < V; v++) acc[0][v] = fma(wide(pr.v[v]), wide(s[v]), acc[0][v]);
         }
     }
     __shared__ double tot[S];
@@ -398,24 +421,24 @@ __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4)))
 }
 
 // ---- K3: x += alpha p, r -= alpha q; r^T r and r^T D^-1 r -> convergence, beta ----
-template <int S>
-__global__ void __launch_bounds__(kBlock) k_update(Args a, double *__restrict__ xx, double *__restrict__ rr,
-                                                   const double *__restrict__ pp, const double *__restrict__ qq,
-                                                   const double *__restrict__ dinv)
+template <typename T, int S>
+__global__ void __launch_bounds__(kBlock) k_update(Args a, T *__restrict__ xx, T *__restrict__ rr,
+                                                   const T *__restrict__ pp, const T *__restrict__ qq,
+                                                   const T *__restrict__ dinv)
 {
-    using LG = VecGeo<S>;
+    using LG = VecGeo<T, S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
     const int e = blockIdx.y;
     if (a.w.ens_live[e] == 0) return;
     const int lane0 = (threadIdx.x % TPR) * V;
     const int L0 = e * S + lane0;
     int lv[V];
-    double al[V];
+    T al[V];
     bool mine = false;
 #pragma unroll
     for (int v = 0; v < V; v++) {
         lv[v] = a.w.live[L0 + v];
-        al[v] = lv[v] ? a.w.alpha[L0 + v] : 0.0;
+        al[v] = lv[v] ? (T)a.w.alpha[L0 + v] : T(0);
         mine = mine || lv[v];
     }
     double acc[2][V] = {};
@@ -424,7 +447,7 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a, double *__restrict__ 
         const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
         for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
             const size_t o = vb + (size_t)r * S;
-            Vec<V> xv, rv, pv, qv, dv;
+            Vec<T, V> xv, rv, pv, qv, dv;
             xv.load(xx + o);
             rv.load(rr + o);
             pv.load_ro(pp + o);
@@ -435,8 +458,9 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a, double *__restrict__ 
                 if (!lv[v]) continue;  // frozen lane: keep x and r
                 xv.v[v] = fma(al[v], pv.v[v], xv.v[v]);
                 rv.v[v] = fma(-al[v], qv.v[v], rv.v[v]);
-                acc[0][v] = fma(rv.v[v], rv.v[v], acc[0][v]);
-                acc[1][v] = fma(rv.v[v], dv.v[v] * rv.v[v], acc[1][v]);
+                const T z = dv.v[v] * rv.v[v];
+                acc[0][v] = fma(wide(rv.v[v]), wide(rv.v[v]), acc[0][v]);
+                acc[1][v] = fma(wide(rv.v[v]), wide(z), acc[1][v]);
             }
             xv.store(xx + o);
             rv.store(rr + o);
@@ -452,9 +476,9 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a, double *__restrict__ 
         if (a.w.live[L]) {
             const int k = a.w.k[L] + 1;
             a.w.k[L] = k;
-            const double rr = tot[threadIdx.x], rzn = tot[S + threadIdx.x];
-            a.w.rr[L] = rr;
-            const double res = sqrt(rr);
+            const double rsq = tot[threadIdx.x], rzn = tot[S + threadIdx.x];
+            a.w.rr[L] = rsq;
+            const double res = sqrt(rsq);
             const double bn = a.w.bnorm[L];
             if (res <= a.rtol * bn) {
                 freeze(a, L, ENS_LANE_CONVERGED, k, res / bn, &dead);
@@ -474,11 +498,11 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a, double *__restrict__ 
 }
 
 // ---- K4: p = D^-1 r + beta p; loop control -------------------------------------
-template <int S>
-__global__ void __launch_bounds__(kBlock) k_direction(Args a, const double *__restrict__ rr,
-                                                      const double *__restrict__ dinv, double *__restrict__ pp)
+template <typename T, int S>
+__global__ void __launch_bounds__(kBlock) k_direction(Args a, const T *__restrict__ rr,
+                                                      const T *__restrict__ dinv, T *__restrict__ pp)
 {
-    using LG = VecGeo<S>;
+    using LG = VecGeo<T, S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
     const int e = blockIdx.y;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
@@ -492,12 +516,12 @@ __global__ void __launch_bounds__(kBlock) k_direction(Args a, const double *__re
     const int lane0 = (threadIdx.x % TPR) * V;
     const int L0 = e * S + lane0;
     int lv[V];
-    double be[V];
+    T be[V];
     bool mine = false;
 #pragma unroll
     for (int v = 0; v < V; v++) {
         lv[v] = a.w.live[L0 + v];
-        be[v] = lv[v] ? a.w.beta[L0 + v] : 0.0;
+        be[v] = lv[v] ? (T)a.w.beta[L0 + v] : T(0);
         mine = mine || lv[v];
     }
     if (!mine) return;
@@ -505,7 +529,7 @@ __global__ void __launch_bounds__(kBlock) k_direction(Args a, const double *__re
     const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
     for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
         const size_t o = vb + (size_t)r * S;
-        Vec<V> rv, dv, pv;
+        Vec<T, V> rv, dv, pv;
         rv.load_ro(rr + o);
         dv.load_ro(dinv + o);
         pv.load(pp + o);
@@ -537,67 +561,44 @@ __global__ void k_spmv_prep(Args a)
     if (L < a.E) a.w.ens_live[L] = a.S;
 }
 
-template <int S>
+template <typename T, int S>
 void launch_spmv(const Args &a, cudaStream_t st)
 {
     dim3 grid(a.g.nblk, a.E);
-    k_spmv<S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, a.vals, a.w.p, a.w.q);
+    k_spmv<T, S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, (const T *)a.vals, (const T *)a.w.p, (T *)a.w.q);
 }
 
-void dispatch_spmv(const Args &a, cudaStream_t st)
-{
-    switch (a.S) {
-    case 1: launch_spmv<1>(a, st); break;
-    case 2: launch_spmv<2>(a, st); break;
-    case 4: launch_spmv<4>(a, st); break;
-    case 8: launch_spmv<8>(a, st); break;
-    case 16: launch_spmv<16>(a, st); break;
-    case 32: launch_spmv<32>(a, st); break;
-    default: launch_spmv<64>(a, st); break;
-    }
-}
-
-template <int S>
+template <typename T, int S>
 void launch_body(const Args &a, cudaStream_t st)
 {
     dim3 grid(a.g.nblk, a.E);
-    k_spmv<S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, a.vals, a.w.p, a.w.q);
-    k_update<S><<<grid, kBlock, 0, st>>>(a, a.x, a.w.r, a.w.p, a.w.q, a.dinv);
-    k_direction<S><<<grid, kBlock, 0, st>>>(a, a.w.r, a.dinv, a.w.p);
+    k_spmv<T, S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, (const T *)a.vals, (const T *)a.w.p, (T *)a.w.q);
+    k_update<T, S><<<grid, kBlock, 0, st>>>(a, (T *)a.x, (T *)a.w.r, (const T *)a.w.p, (const T *)a.w.q,
+                                           (const T *)a.dinv);
+    k_direction<T, S><<<grid, kBlock, 0, st>>>(a, (const T *)a.w.r, (const T *)a.dinv, (T *)a.w.p);
 }
 
-template <int S>
+template <typename T, int S>
 void launch_init(const Args &a, cudaStream_t st)
 {
     dim3 grid(a.g.nblk, a.E);
-    k_init<S><<<grid, kBlock, 0, st>>>(a, a.b, a.dinv, a.x, a.w.r, a.w.p);
+    k_init<T, S><<<grid, kBlock, 0, st>>>(a, a.b, (const T *)a.dinv, (T *)a.x, (T *)a.w.r, (T *)a.w.p);
 }
 
-void dispatch_body(const Args &a, cudaStream_t st)
-{
-    switch (a.S) {
-    case 1: launch_body<1>(a, st); break;
-    case 2: launch_body<2>(a, st); break;
-    case 4: launch_body<4>(a, st); break;
-    case 8: launch_body<8>(a, st); break;
-    case 16: launch_body<16>(a, st); break;
-    case 32: launch_body<32>(a, st); break;
-    default: launch_body<64>(a, st); break;
+#define ENS_DISPATCH_S(FN, T, a, st)          \
+    switch ((a).S) {                          \
+    case 1: FN<T, 1>(a, st); break;           \
+    case 2: FN<T, 2>(a, st); break;           \
+    case 4: FN<T, 4>(a, st); break;           \
+    case 8: FN<T, 8>(a, st); break;           \
+    case 16: FN<T, 16>(a, st); break;         \
+    case 32: FN<T, 32>(a, st); break;         \
+    default: FN<T, 64>(a, st); break;         \
     }
-}
 
-void dispatch_init(const Args &a, cudaStream_t st)
-{
-    switch (a.S) {
-    case 1: launch_init<1>(a, st); break;
-    case 2: launch_init<2>(a, st); break;
-    case 4: launch_init<4>(a, st); break;
-    case 8: launch_init<8>(a, st); break;
-    case 16: launch_init<16>(a, st); break;
-    case 32: launch_init<32>(a, st); break;
-    default: launch_init<64>(a, st); break;
-    }
-}
+template <typename T> void dispatch_body(const Args &a, cudaStream_t st) { ENS_DISPATCH_S(launch_body, T, a, st) }
+template <typename T> void dispatch_init(const Args &a, cudaStream_t st) { ENS_DISPATCH_S(launch_init, T, a, st) }
+template <typename T> void dispatch_spmv(const Args &a, cudaStream_t st) { ENS_DISPATCH_S(launch_spmv, T, a, st) }
 
 uint64_t bits(const void *p) { return (uint64_t)(uintptr_t)p; }
 uint64_t bits(double d)
@@ -608,13 +609,14 @@ uint64_t bits(double d)
 }
 
 // Instantiate (or reuse) the while-loop graph for these arguments.
+template <typename T>
 int loop_graph(ens_ctx *h, Args a, cudaGraphExec_t *out)
 {
     std::vector<uint64_t> key = {bits(a.rowptr), bits(a.colidx), bits(a.vals), bits(a.dinv), bits(a.b),
                                  bits(a.x), bits(a.active), bits(a.iters), bits(a.status), bits(a.relres),
-                                 bits(a.w.r), (uint64_t)a.J, (uint64_t)a.S, (uint64_t)a.E,
-                                 (uint64_t)a.maxit, (uint64_t)a.nnz, bits(a.rtol),
-                                 (uint64_t)a.g.nblk, (uint64_t)a.g.RT};
+                                 bits(a.w.r), bits(a.w.part0), bits(a.w.live), (uint64_t)a.J, (uint64_t)a.S,
+                                 (uint64_t)a.E, (uint64_t)a.maxit, (uint64_t)a.nnz, bits(a.rtol),
+                                 (uint64_t)a.g.nblk, (uint64_t)a.g.RT, (uint64_t)sizeof(T)};
     h->clock++;
     for (auto &ge : h->graphs)
         if (ge.key == key) {
@@ -648,7 +650,7 @@ int loop_graph(ens_ctx *h, Args a, cudaGraphExec_t *out)
         cudaGraphDestroy(g);
         return cuda_error(h, e, "cudaStreamBeginCaptureToGraph");
     }
-    dispatch_body(a, h->capture);
+    dispatch_body<T>(a, h->capture);
     cudaError_t le = cudaGetLastError();
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(h->capture, &captured);
@@ -681,6 +683,46 @@ int loop_graph(ens_ctx *h, Args a, cudaGraphExec_t *out)
     return ENS_OK;
 }
 
+// Run the whole PCG (init, loop, finish) for prepared arguments.
+template <typename T>
+int run_solve(ens_ctx *h, const Args &a, cudaStream_t st, bool host_loop)
+{
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)a.E * CNT_KINDS * sizeof(int), st));
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl, 0, 2 * sizeof(int), st));
+    dispatch_init<T>(a, st);
+    ENS_LAUNCH_CHECK(h, "PCG init kernel");
+    if (host_loop) {
+        // Same kernels launched from the host, with the live count read back
+        // every 16 trips (profilers see each launch; the graph path does not
+        // expose kernels inside a conditional body to them).
+        int ctl[2] = {1, 0};
+        while (ctl[0] > 0 && ctl[1] < a.maxit) {
+            for (int t = 0; t < 16; t++) dispatch_body<T>(a, st);
+            ENS_LAUNCH_CHECK(h, "PCG loop kernels");
+            ENS_CUDA_CHECK(h, cudaMemcpyAsync(ctl, a.w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+            ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+        }
+    } else {
+        cudaGraphExec_t exec;
+        int rc = loop_graph<T>(h, a, &exec);
+        if (rc) return rc;
+        ENS_CUDA_CHECK(h, cudaGraphLaunch(exec, st));
+    }
+    k_finish<<<(a.E * a.S + 255) / 256, 256, 0, st>>>(a);
+    ENS_LAUNCH_CHECK(h, "PCG finish kernel");
+    return ENS_OK;
+}
+
+int check_solve_args(ens_ctx *h, const char *who, int J, int64_t nnz, int S, int E, double rtol, int maxit)
+{
+    if (!lane_count_ok(S)) return set_error(h, ENS_EINVAL, std::string(who) + ": S must be 1,2,4,...,64");
+    if (J <= 0 || nnz <= 0 || E < 0 || nnz >= (1LL << 31))
+        return set_error(h, ENS_EINVAL, std::string(who) + ": bad J / nnz / E");
+    if (E > 65535) return set_error(h, ENS_EINVAL, std::string(who) + ": E > 65535");
+    if (!(rtol >= 0.0) || maxit < 0) return set_error(h, ENS_EINVAL, std::string(who) + ": bad rtol / maxit");
+    return ENS_OK;
+}
+
 }  // namespace
 }  // namespace ens
 
@@ -699,11 +741,9 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
                              double *relres, int32_t *status, void *work, size_t work_bytes, void *stream)
 {
     if (!h) return ENS_EINVAL;
-    if (!lane_count_ok(S)) return set_error(h, ENS_EINVAL, "ens_pcg_solve: S must be 1,2,4,...,64");
-    if (J <= 0 || nnz <= 0 || E < 0 || nnz >= (1LL << 31))
-        return set_error(h, ENS_EINVAL, "ens_pcg_solve: bad J / nnz / E");
+    int rc = check_solve_args(h, "ens_pcg_solve", J, nnz, S, E, rtol, maxit);
+    if (rc) return rc;
     if (E == 0) return ENS_OK;
-    if (!(rtol >= 0.0) || maxit < 0) return set_error(h, ENS_EINVAL, "ens_pcg_solve: bad rtol / maxit");
     if (!rowptr || !colidx || !vals || !dinv || !b || !x || !iters || !relres || !status || !work)
         return set_error(h, ENS_EINVAL, "ens_pcg_solve: null pointer");
     if (((uintptr_t)vals | (uintptr_t)dinv | (uintptr_t)b | (uintptr_t)x | (uintptr_t)work) & 15)
@@ -718,30 +758,299 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
     a.rowptr = rowptr; a.colidx = colidx; a.vals = vals; a.dinv = dinv; a.b = b; a.x = x;
     a.active = active; a.iters = iters; a.status = status; a.relres = relres;
     layout(J, S, E, g, &a.w, (char *)work);
-    cudaStream_t st = (cudaStream_t)stream;
-    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
-    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl, 0, CTL_WORDS * sizeof(int), st));
-    dispatch_init(a, st);
-    ENS_LAUNCH_CHECK(h, "ens_pcg_solve: init kernel");
-    if (h->host_loop) {
-        // Same kernels launched from the host, with the live count read back
-        // every 16 trips (profilers see each launch; the graph path does not
-        // expose kernels inside a conditional body to them).
-        int ctl[2] = {1, 0};
-        while (ctl[0] > 0 && ctl[1] < maxit) {
-            for (int t = 0; t < 16; t++) dispatch_body(a, st);
-            ENS_LAUNCH_CHECK(h, "ens_pcg_solve: loop kernels");
-            ENS_CUDA_CHECK(h, cudaMemcpyAsync(ctl, a.w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
-            ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
-        }
-    } else {
-        cudaGraphExec_t exec;
-        int rc = loop_graph(h, a, &exec);
-        if (rc) return rc;
-        ENS_CUDA_CHECK(h, cudaGraphLaunch(exec, st));
+    return run_solve<double>(h, a, (cudaStream_t)stream, h->host_loop != 0);
+}
+
+// ---- mixed precision: FP32 inner PCG inside FP64 iterative refinement ---------
+// r = b - A64 x in FP64; stop a lane when ||r|| <= rtol ||b||; else solve
+// A32 d = r with the FP32 form of the loop above (to ||r - A32 d|| <= rtol_inner ||r||,
+// FP64 inner products and scalars) and update x += d in FP64.
+namespace ens {
+namespace {
+
+struct IrWs {
+    Ws inner;            // FP32 loop workspace
+    double *r64;         // [E][J][S] outer residual
+    float *dinv32, *d32; // [E][J][S]
+    double *bnorm;       // [E][S] ||b||
+    int *olive, *oits, *inner_tot;  // [E][S]
+    uint8_t *iactive;    // [E][S] lanes the next inner solve works on
+    int32_t *istatus, *iiters;  // [E][S] inner outcome
+    double *irelres;     // [E][S]
+};
+
+size_t ir_layout(int J, int S, int E, const Geo &g, IrWs *w, char *base)
+{
+    Bump m(base);
+    IrWs t;
+    lay_loop(m, J, S, E, g, sizeof(float), &t.inner);
+    size_t vec = (size_t)E * J * S;
+    size_t lane = (size_t)E * S;
+    t.r64 = (double *)m.take(vec * 8);
+    t.dinv32 = (float *)m.take(vec * 4);
+    t.d32 = (float *)m.take(vec * 4);
+    t.bnorm = (double *)m.take(lane * 8);
+    t.olive = (int *)m.take(lane * 4);
+    t.oits = (int *)m.take(lane * 4);
+    t.inner_tot = (int *)m.take(lane * 4);
+    t.iactive = (uint8_t *)m.take(lane);
+    t.istatus = (int32_t *)m.take(lane * 4);
+    t.iiters = (int32_t *)m.take(lane * 4);
+    t.irelres = (double *)m.take(lane * 8);
+    if (w) *w = t;
+    return m.off;
+}
+
+struct IrArgs {
+    int J, S, E, maxit_outer;
+    long long nnz;
+    double rtol;
+    Geo g;
+    const uint8_t *active;
+    int32_t *iters, *outer_its, *status;
+    double *relres;
+    IrWs w;
+};
+
+// x = 0, D^-1 in FP32, outer lane state.
+__global__ void k_ir_prep(IrArgs a, const double *__restrict__ dinv, double *__restrict__ x)
+{
+    const size_t n = (size_t)a.E * a.J * a.S;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        x[i] = 0.0;
+        a.w.dinv32[i] = (float)dinv[i];
     }
-    k_finish<<<(E * S + 255) / 256, 256, 0, st>>>(a);
-    ENS_LAUNCH_CHECK(h, "ens_pcg_solve: finish kernel");
+    const int lanes = a.E * a.S;
+    for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < lanes; L += gridDim.x * blockDim.x) {
+        const int act = a.active ? (int)a.active[L] : 1;
+        a.w.olive[L] = act;
+        a.w.oits[L] = 0;
+        a.w.inner_tot[L] = 0;
+        a.status[L] = act ? ENS_LANE_MAXIT : ENS_LANE_INACTIVE;
+        a.iters[L] = 0;
+        a.outer_its[L] = 0;
+        a.relres[L] = act ? 1.0 : 0.0;
+    }
+}
+
+// r = b - A64 x (FP64) and ||r||^2 per lane -> outer convergence.
+template <int S>
+__global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4)))
+    k_residual(IrArgs a, Args sa, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+               const double *__restrict__ vals_all, const double *__restrict__ x_all,
+               const double *__restrict__ b_all, double *__restrict__ r_all)
+{
+    using LG = SpmvGeo<S>;
+    constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
+    const int e = blockIdx.y;
+    const int lane0 = (threadIdx.x % TPR) * V;
+    const int L0 = e * S + lane0;
+    bool mine = a.w.olive[L0] != 0;
+    if (V == 2) mine = mine || a.w.olive[L0 + 1] != 0;
+    double acc[1][V] = {};
+    if (mine) {
+        const double *__restrict__ vals = vals_all + (size_t)e * a.nnz * S + lane0;
+        const double *__restrict__ x = x_all + (size_t)e * a.J * S + lane0;
+        const double *__restrict__ bb = b_all + (size_t)e * a.J * S + lane0;
+        double *__restrict__ r = r_all + (size_t)e * a.J * S + lane0;
+        const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
+        for (int row = r0 + threadIdx.x / TPR; row < r1; row += RPP) {
+            const int k0 = __ldg(rowptr + row), k1 = __ldg(rowptr + row + 1);
+            double s[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) s[v] = 0.0;
+            for (int kb = k0; kb < k1; kb += kChunk) {
+                int c[kChunk];
+                Vec<double, V> av[kChunk], xv[kChunk];
+#pragma unroll
+                for (int u = 0; u < kChunk; u++)
+                    if (kb + u < k1) c[u] = __ldg(colidx + kb + u);
+#pragma unroll
+                for (int u = 0; u < kChunk; u++)
+                    if (kb + u < k1) {
+                        av[u].load_stream(vals + (size_t)(kb + u) * S);
+                        xv[u].load_ro(x + (size_t)c[u] * S);
+                    }
+#pragma unroll
+                for (int u = 0; u < kChunk; u++)
+                    if (kb + u < k1) {
+#pragma unroll
+                        for (int v = 0; v < V; v++) s[v] = fma(av[u].v[v], xv[u].v[v], s[v]);
+                    }
+            }
+            Vec<double, V> bv, rv;
+            bv.load_ro(bb + (size_t)row * S);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                rv.v[v] = bv.v[v] - s[v];
+                acc[0][v] = fma(rv.v[v], rv.v[v], acc[0][v]);
+            }
+            rv.store(r + (size_t)row * S);
+        }
+    }
+    __shared__ double tot[S];
+    __shared__ int live_cnt;
+    if (threadIdx.x == 0) live_cnt = 0;
+    double *parts[1] = {sa.w.part0};
+    if (!reduce_lanes<LG, S, 1>(acc, parts, e, a.g.nblk, sa.w.counter + e * CNT_KINDS + CNT_RES, tot)) return;
+    if (threadIdx.x < S) {
+        const int L = e * S + threadIdx.x;
+        int go = 0;
+        if (a.w.olive[L]) {
+            const double rn = sqrt(tot[threadIdx.x]);
+            const int it = a.w.oits[L];
+            if (it == 0) a.w.bnorm[L] = rn;  // x = 0 on the first pass: r = b
+            const double bn = a.w.bnorm[L];
+            a.iters[L] = a.w.inner_tot[L];
+            a.outer_its[L] = it;
+            if (!isfinite(rn)) {
+                a.w.olive[L] = 0;
+                a.status[L] = it == 0 ? ENS_LANE_BADINPUT : ENS_LANE_BREAKDOWN;
+                a.relres[L] = __longlong_as_double(0x7ff8000000000000LL);
+            } else if (bn == 0.0) {
+                a.w.olive[L] = 0;
+                a.status[L] = ENS_LANE_CONVERGED;
+                a.relres[L] = 0.0;
+            } else if (rn <= a.rtol * bn) {
+                a.w.olive[L] = 0;
+                a.status[L] = ENS_LANE_CONVERGED;
+                a.relres[L] = rn / bn;
+            } else if (it >= a.maxit_outer) {
+                a.w.olive[L] = 0;
+                a.status[L] = ENS_LANE_MAXIT;
+                a.relres[L] = rn / bn;
+            } else {
+                a.relres[L] = rn / bn;
+                go = 1;
+            }
+        }
+        a.w.iactive[L] = (uint8_t)go;
+        if (go) atomicAdd(&live_cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && live_cnt) atomicAdd(sa.w.ctl + CTL_OUTER_LIVE, live_cnt);
+}
+
+// x += d (FP64) for the lanes of the inner solve.
+template <int S>
+__global__ void k_ir_update(IrArgs a, double *__restrict__ x, const float *__restrict__ d)
+{
+    const size_t n = (size_t)a.E * a.J * S;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int L = (int)((i / ((size_t)a.J * S)) * S + i % S);
+        if (a.w.iactive[L]) x[i] = x[i] + (double)d[i];
+    }
+}
+
+// Outer bookkeeping after an inner solve.
+__global__ void k_ir_lanes(IrArgs a)
+{
+    const int lanes = a.E * a.S;
+    for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < lanes; L += gridDim.x * blockDim.x) {
+        if (!a.w.iactive[L]) continue;
+        a.w.oits[L] += 1;
+        a.w.inner_tot[L] += a.w.iiters[L];
+        const int st = a.w.istatus[L];
+        if ((st == ENS_LANE_BREAKDOWN && a.w.iiters[L] == 0) || st == ENS_LANE_BADINPUT) {
+            a.w.olive[L] = 0;  // no progress possible: keep x
+            a.status[L] = ENS_LANE_BREAKDOWN;
+            a.iters[L] = a.w.inner_tot[L];
+            a.outer_its[L] = a.w.oits[L];
+        }
+    }
+}
+
+template <int S>
+void launch_residual(const IrArgs &ia, const Args &sa, const double *vals, const double *x, const double *b,
+                     cudaStream_t st)
+{
+    dim3 grid(ia.g.nblk, ia.E);
+    k_residual<S><<<grid, kBlock, 0, st>>>(ia, sa, sa.rowptr, sa.colidx, vals, x, b, ia.w.r64);
+}
+
+template <int S>
+void launch_ir_update(const IrArgs &ia, double *x, cudaStream_t st)
+{
+    k_ir_update<S><<<152 * 4, 256, 0, st>>>(ia, x, ia.w.d32);
+}
+
+}  // namespace
+}  // namespace ens
+
+extern "C" size_t ens_pcg_ir_workspace_size(int J, int64_t nnz, int S, int E)
+{
+    (void)nnz;
+    if (J <= 0 || E <= 0 || !lane_count_ok(S)) return 0;
+    return ir_layout(J, S, E, geometry(J, S), nullptr, nullptr);
+}
+
+extern "C" int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E, const int32_t *rowptr,
+                                const int32_t *colidx, const double *vals, const float *vals32, const double *dinv,
+                                const double *b, double *x, const uint8_t *active, double rtol, double rtol_inner,
+                                int maxit_inner, int maxit_outer, int32_t *iters, int32_t *outer_its,
+                                double *relres, int32_t *status, void *work, size_t work_bytes, void *stream)
+{
+    if (!h) return ENS_EINVAL;
+    int rc = check_solve_args(h, "ens_pcg_solve_ir", J, nnz, S, E, rtol, maxit_inner);
+    if (rc) return rc;
+    if (!(rtol_inner > 0.0 && rtol_inner < 1.0) || maxit_outer < 0)
+        return set_error(h, ENS_EINVAL, "ens_pcg_solve_ir: need 0 < rtol_inner < 1 and maxit_outer >= 0");
+    if (E == 0) return ENS_OK;
+    if (!rowptr || !colidx || !vals || !vals32 || !dinv || !b || !x || !iters || !outer_its || !relres || !status ||
+        !work)
+        return set_error(h, ENS_EINVAL, "ens_pcg_solve_ir: null pointer");
+    if (((uintptr_t)vals | (uintptr_t)vals32 | (uintptr_t)dinv | (uintptr_t)b | (uintptr_t)x | (uintptr_t)work) & 15)
+        return set_error(h, ENS_EINVAL, "ens_pcg_solve_ir: arrays must be 16-byte aligned");
+    Geo g = geometry(J, S);
+    const size_t need = ir_layout(J, S, E, g, nullptr, nullptr);
+    if (work_bytes < need)
+        return set_error(h, ENS_ENOMEM, "ens_pcg_solve_ir: workspace too small (need " + std::to_string(need) + " bytes)");
+    cudaStream_t st = (cudaStream_t)stream;
+    IrArgs ia;
+    memset(&ia, 0, sizeof(ia));
+    ia.J = J; ia.S = S; ia.E = E; ia.maxit_outer = maxit_outer; ia.nnz = nnz; ia.rtol = rtol; ia.g = g;
+    ia.active = active; ia.iters = iters; ia.outer_its = outer_its; ia.status = status; ia.relres = relres;
+    ir_layout(J, S, E, g, &ia.w, (char *)work);
+    // the inner FP32 solve: b = the FP64 residual, x = the FP32 correction
+    Args sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.J = J; sa.S = S; sa.E = E; sa.maxit = maxit_inner; sa.nnz = nnz; sa.rtol = rtol_inner; sa.g = g;
+    sa.rowptr = rowptr; sa.colidx = colidx; sa.vals = vals32; sa.dinv = ia.w.dinv32; sa.b = ia.w.r64;
+    sa.x = ia.w.d32; sa.active = ia.w.iactive; sa.iters = ia.w.iiters; sa.status = ia.w.istatus;
+    sa.relres = ia.w.irelres; sa.w = ia.w.inner;
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(sa.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
+    k_ir_prep<<<152 * 4, 256, 0, st>>>(ia, dinv, x);
+    ENS_LAUNCH_CHECK(h, "ens_pcg_solve_ir: prep");
+    for (int it = 0; it <= maxit_outer; it++) {
+        ENS_CUDA_CHECK(h, cudaMemsetAsync(sa.w.ctl + CTL_OUTER_LIVE, 0, sizeof(int), st));
+        switch (S) {
+        case 1: launch_residual<1>(ia, sa, vals, x, b, st); break;
+        case 2: launch_residual<2>(ia, sa, vals, x, b, st); break;
+        case 4: launch_residual<4>(ia, sa, vals, x, b, st); break;
+        case 8: launch_residual<8>(ia, sa, vals, x, b, st); break;
+        case 16: launch_residual<16>(ia, sa, vals, x, b, st); break;
+        case 32: launch_residual<32>(ia, sa, vals, x, b, st); break;
+        default: launch_residual<64>(ia, sa, vals, x, b, st); break;
+        }
+        ENS_LAUNCH_CHECK(h, "ens_pcg_solve_ir: residual");
+        int olive = 0;
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(&olive, sa.w.ctl + CTL_OUTER_LIVE, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+        if (olive == 0) break;
+        rc = run_solve<float>(h, sa, st, h->host_loop != 0);
+        if (rc) return rc;
+        switch (S) {
+        case 1: launch_ir_update<1>(ia, x, st); break;
+        case 2: launch_ir_update<2>(ia, x, st); break;
+        case 4: launch_ir_update<4>(ia, x, st); break;
+        case 8: launch_ir_update<8>(ia, x, st); break;
+        case 16: launch_ir_update<16>(ia, x, st); break;
+        case 32: launch_ir_update<32>(ia, x, st); break;
+        default: launch_ir_update<64>(ia, x, st); break;
+        }
+        k_ir_lanes<<<(E * S + 255) / 256, 256, 0, st>>>(ia);
+        ENS_LAUNCH_CHECK(h, "ens_pcg_solve_ir: update");
+    }
     return ENS_OK;
 }
 
@@ -783,11 +1092,9 @@ extern "C" int ens_pcg_solve_static(ens_handle h, int J, int64_t nnz, int S, int
                                     const double *b, double *x, const uint8_t *active, double rtol, int maxit,
                                     int32_t *iters, double *relres, int32_t *status, void *stream)
 {
-    if (!lane_count_ok(S)) return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: S must be 1,2,4,...,64");
-    if (J <= 0 || nnz <= 0 || E < 0 || nnz >= (1LL << 31))
-        return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: bad J / nnz / E");
+    int rc = check_solve_args(h, "ens_pcg_solve_static", J, nnz, S, E, rtol, maxit);
+    if (rc) return rc;
     if (E == 0) return ENS_OK;
-    if (!(rtol >= 0.0) || maxit < 0) return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: bad rtol / maxit");
     if (!rowptr || !colidx || !vals || !dinv || !b || !x || !iters || !relres || !status)
         return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: null pointer");
     if (((uintptr_t)vals | (uintptr_t)dinv | (uintptr_t)b | (uintptr_t)x) & 15)
@@ -799,7 +1106,7 @@ extern "C" int ens_pcg_solve_static(ens_handle h, int J, int64_t nnz, int S, int
                                             " bytes of scratch; the static scratch holds " +
                                             std::to_string(kStaticScratchBytes) + " (use ens_pcg_solve)");
     void *scratch = nullptr;
-    int rc = scratch_address(h, &scratch);
+    rc = scratch_address(h, &scratch);
     if (rc) return rc;
     Args a;
     memset(&a, 0, sizeof(a));
@@ -807,23 +1114,9 @@ extern "C" int ens_pcg_solve_static(ens_handle h, int J, int64_t nnz, int S, int
     a.rowptr = rowptr; a.colidx = colidx; a.vals = vals; a.dinv = dinv; a.b = b; a.x = x;
     a.active = active; a.iters = iters; a.status = status; a.relres = relres;
     layout(J, S, E, g, &a.w, (char *)scratch);
-    cudaStream_t st = (cudaStream_t)stream;
-    // The array keeps the previous call's contents: the counters and the loop
-    // control start from zero here; everything else is written before it is read.
-    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
-    ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl, 0, CTL_WORDS * sizeof(int), st));
-    dispatch_init(a, st);
-    ENS_LAUNCH_CHECK(h, "ens_pcg_solve_static: init kernel");
-    int ctl[2] = {1, 0};
-    while (ctl[0] > 0 && ctl[1] < maxit) {
-        for (int t = 0; t < 16; t++) dispatch_body(a, st);
-        ENS_LAUNCH_CHECK(h, "ens_pcg_solve_static: loop kernels");
-        ENS_CUDA_CHECK(h, cudaMemcpyAsync(ctl, a.w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
-        ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
-    }
-    k_finish<<<(E * S + 255) / 256, 256, 0, st>>>(a);
-    ENS_LAUNCH_CHECK(h, "ens_pcg_solve_static: finish kernel");
-    return ENS_OK;
+    // The array keeps the previous call's contents: run_solve clears the
+    // counters and the loop control; everything else is written before it is read.
+    return run_solve<double>(h, a, (cudaStream_t)stream, true);
 }
 
 extern "C" int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const int32_t *rowptr,
@@ -832,7 +1125,8 @@ extern "C" int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const in
 {
     if (!h) return ENS_EINVAL;
     if (!lane_count_ok(S)) return set_error(h, ENS_EINVAL, "ens_spmv: S must be 1,2,4,...,64");
-    if (J <= 0 || nnz <= 0 || E < 0 || nnz >= (1LL << 31)) return set_error(h, ENS_EINVAL, "ens_spmv: bad sizes");
+    if (J <= 0 || nnz <= 0 || E < 0 || E > 65535 || nnz >= (1LL << 31))
+        return set_error(h, ENS_EINVAL, "ens_spmv: bad sizes");
     if (E == 0) return ENS_OK;
     if (!rowptr || !colidx || !vals || !p || !q || !work) return set_error(h, ENS_EINVAL, "ens_spmv: null pointer");
     if (((uintptr_t)vals | (uintptr_t)p | (uintptr_t)q | (uintptr_t)work) & 15)
@@ -852,7 +1146,7 @@ extern "C" int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const in
     ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
     k_spmv_prep<<<(E * S + 255) / 256, 256, 0, st>>>(a);
     ENS_LAUNCH_CHECK(h, "ens_spmv: prep");
-    dispatch_spmv(a, st);
+    dispatch_spmv<double>(a, st);
     ENS_LAUNCH_CHECK(h, "ens_spmv: kernel");
     return ENS_OK;
 }

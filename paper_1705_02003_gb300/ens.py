@@ -24,7 +24,8 @@ LANE_CONVERGED, LANE_MAXIT, LANE_BREAKDOWN, LANE_BADINPUT, LANE_INACTIVE = 0, 1,
 EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "ens_pattern",
            "ens_assemble", "ens_pcg_workspace_size", "ens_pcg_solve", "ens_group", "ens_sort_chunk",
            "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv",
-           "ens_pcg_solve_static")
+           "ens_pcg_solve_static", "ens_pcg_ir_workspace_size", "ens_pcg_solve_ir",
+           "ens_adjoint_workspace_size", "ens_adjoint_grad")
 
 _lib = None
 _lock = threading.Lock()
@@ -77,6 +78,13 @@ def _declare(L):
     L.ens_sg_eval.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_int, vp, vp, vp, vp]
     L.ens_qoi.argtypes = [vp, c.c_int, c.c_int, c.c_int, vp, vp, vp, vp]
     L.ens_spmv.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_adjoint_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
+    L.ens_adjoint_workspace_size.restype = c.c_size_t
+    L.ens_adjoint_grad.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_pcg_ir_workspace_size.argtypes = [c.c_int, c.c_int64, c.c_int, c.c_int]
+    L.ens_pcg_ir_workspace_size.restype = c.c_size_t
+    L.ens_pcg_solve_ir.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp, vp,
+                                   c.c_double, c.c_double, c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
     L.ens_pcg_solve_static.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp,
                                        c.c_double, c.c_int, vp, vp, vp, vp]
     i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
@@ -221,6 +229,45 @@ def ens_spmv(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx, vals, 
     rc = load().ens_spmv(h.ptr, int(J), int(nnz), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
                          _ptr(p), _ptr(q), _ptr(pq), _ptr(work), work.numel(), _stream(stream))
     h.check(rc, "ens_spmv")
+
+
+def ens_pcg_ir_workspace_size(J: int, nnz: int, S: int, E: int) -> int:
+    return int(load().ens_pcg_ir_workspace_size(int(J), int(nnz), int(S), int(E)))
+
+
+def ens_pcg_solve_ir(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx, vals, vals32, dinv, b, x,
+                     active, rtol: float, rtol_inner: float, maxit_inner: int, maxit_outer: int, iters,
+                     outer_its, relres, status, work, stream=None):
+    """FP32 inner Jacobi-PCG inside FP64 iterative refinement (see include/ens.h)."""
+    for t, nm, dt in ((vals, "vals", torch.float64), (vals32, "vals32", torch.float32),
+                      (dinv, "dinv", torch.float64), (b, "b", torch.float64), (x, "x", torch.float64),
+                      (iters, "iters", torch.int32), (outer_its, "outer_its", torch.int32),
+                      (relres, "relres", torch.float64), (status, "status", torch.int32)):
+        _check_dtype(t, dt, nm)
+    if vals.numel() != E * nnz * S or vals32.numel() != E * nnz * S or x.numel() != E * J * S:
+        raise ValueError("array sizes do not match E, J, nnz, S")
+    rc = load().ens_pcg_solve_ir(h.ptr, int(J), int(nnz), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                                 _ptr(vals32), _ptr(dinv), _ptr(b), _ptr(x), _ptr(active), float(rtol),
+                                 float(rtol_inner), int(maxit_inner), int(maxit_outer), _ptr(iters),
+                                 _ptr(outer_its), _ptr(relres), _ptr(status), _ptr(work), work.numel(),
+                                 _stream(stream))
+    h.check(rc, "ens_pcg_solve_ir")
+
+
+def ens_adjoint_workspace_size(prob: Problem, S: int, E: int) -> int:
+    return int(load().ens_adjoint_workspace_size(ctypes.byref(prob), int(S), int(E)))
+
+
+def ens_adjoint_grad(h: Handle, prob: Problem, S: int, E: int, xi, u, lam, grad, work, stream=None):
+    """grad[E][S][N] = -lam^T (dA/dxi) u per lane."""
+    J, _ = ens_problem_size(prob)
+    for t, nm in ((xi, "xi"), (u, "u"), (lam, "lam"), (grad, "grad")):
+        _check_dtype(t, torch.float64, nm)
+    if u.numel() != E * J * S or lam.numel() != E * J * S or grad.numel() != E * S * prob.nparam:
+        raise ValueError("u / lam / grad sizes do not match E, J, S, nparam")
+    rc = load().ens_adjoint_grad(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(xi), _ptr(u), _ptr(lam),
+                                 _ptr(grad), _ptr(work), work.numel(), _stream(stream))
+    h.check(rc, "ens_adjoint_grad")
 
 
 STATIC_SCRATCH_BYTES = 8 << 20

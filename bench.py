@@ -240,7 +240,7 @@ def run_ours(args, wl):
     extra = {}
     if not args.no_arms:
         # the other groupings and one-sample-at-a-time PCG, one step each
-        for arm in ("nat", "rand"):
+        for arm in ("par", "nat", "rand"):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -260,6 +260,8 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         tp = e0.elapsed_time(e1) / 1e3
         extra["per_sample"] = {"value": M / tp, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r3["I"] - run["I"])))}
+
+    layers = {} if args.no_layers else run_layers(h, stream)
 
     # dominant kernel: the ensemble SpMV (K2) on a full-capacity batch
     sol = ad.solver
@@ -360,6 +362,7 @@ def run_ours(args, wl):
             "clocks": clk,
             "R": {"sur": R["run"][1], "its": R["its"][1]},
             "arms": extra,
+            "layers": layers,
         }
         if "per_sample" in extra:
             line["speedup_vs_per_sample"] = value / extra["per_sample"]["value"]
@@ -367,6 +370,81 @@ def run_ours(args, wl):
         print(json.dumps(line))
     h.close()
     return 0
+
+
+def run_layers(h, stream):
+    """The three system layers on bounded samples of their workloads (one
+    ensemble each): FP32-in-FP64 refinement vs the FP64 solve on the 128^3
+    problem, the adjoint gradient on the 512^2 problem."""
+    import torch
+
+    from paper_1705_02003_gb300 import adjoint, ens, inputs
+    from paper_1705_02003_gb300.solver import EnsembleSolver
+
+    out = {}
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    # precision layer
+    wl = inputs.WORKLOADS["fd7_128_mixed"]
+    prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    sol = EnsembleSolver(h, prob, wl.S, wl.S, wl.rtol, wl.maxit)
+    xi = torch.from_numpy(inputs.draws(wl.S, wl.nparam, seed=wl.seed)).cuda()
+    J, nnz, S = sol.J, sol.nnz, sol.S
+    ens.ens_assemble(h, prob, S, 1, xi.reshape(-1), sol.rowptr, sol.colidx, sol.vals, sol.dinv, sol.b)
+    v32 = torch.empty(nnz * S, dtype=torch.float32, device="cuda")
+    ens.ens_assemble(h, prob, S, 1, xi.reshape(-1), sol.rowptr, sol.colidx, v32)
+    x64 = torch.empty(J * S, dtype=torch.float64, device="cuda")
+    it64 = torch.empty(S, dtype=torch.int32, device="cuda")
+    st64 = torch.empty_like(it64)
+    rr64 = torch.empty(S, dtype=torch.float64, device="cuda")
+    _, t64 = timed(lambda: ens.ens_pcg_solve(h, J, nnz, S, 1, sol.rowptr, sol.colidx, sol.vals, sol.dinv, sol.b,
+                                             x64, None, wl.rtol, wl.maxit, it64, rr64, st64, sol.work))
+    xir = torch.empty(J * S, dtype=torch.float64, device="cuda")
+    itir = torch.empty(S, dtype=torch.int32, device="cuda")
+    oit = torch.empty_like(itir)
+    stir = torch.empty_like(itir)
+    rrir = torch.empty(S, dtype=torch.float64, device="cuda")
+    wir = torch.empty(ens.ens_pcg_ir_workspace_size(J, nnz, S, 1), dtype=torch.uint8, device="cuda")
+    _, tir = timed(lambda: ens.ens_pcg_solve_ir(h, J, nnz, S, 1, sol.rowptr, sol.colidx, sol.vals, v32, sol.dinv,
+                                                sol.b, xir, None, wl.rtol, 1e-6, wl.maxit, 50, itir, oit, rrir,
+                                                stir, wir))
+    d = (xir - x64).view(J, S)
+    err = (d.norm(dim=0) / x64.view(J, S).norm(dim=0)).max().item()
+    out["precision"] = {
+        "workload": wl.name, "sample": f"one ensemble of {S} draws",
+        "fp64_value": S / t64, "ir_value": S / tir, "unit": "sample-solves/s", "speedup": t64 / tir,
+        "fp64_max_iters": int(it64.max().item()), "ir_inner_iters_max": int(itir.max().item()),
+        "ir_outer_max": int(oit.max().item()), "max_relres": float(rrir.max().item()),
+        "max_rel_error_vs_fp64": err,
+        "all_converged": bool((stir == 0).all().item() and (st64 == 0).all().item())}
+    del sol, v32, wir, x64, xir
+    torch.cuda.empty_cache()
+
+    # differentiation layer
+    wl = inputs.WORKLOADS["fd5_512_adjoint"]
+    prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    w = torch.from_numpy(inputs.region_weights(wl.n, 2))
+    asol = adjoint.AdjointSolver(h, prob, wl.S, wl.S, w, wl.rtol, wl.maxit)
+    xi = torch.from_numpy(inputs.draws(wl.S, wl.nparam, seed=wl.seed)).cuda()
+    _, tf = timed(lambda: asol.forward(xi))
+    _, tg = timed(lambda: asol.gradient(xi, recompute_forward=False))
+    out["differentiation"] = {
+        "workload": wl.name, "sample": f"one ensemble of {wl.S} draws",
+        "forward_value": wl.S / tf, "gradient_value": wl.S / (tf + tg), "unit": "samples/s (Q and dQ/dxi)",
+        "forward_max_iters": int(asol.last["forward_iters"].max().item()),
+        "adjoint_max_iters": int(asol.last["adjoint_iters"].max().item())}
+    del asol
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_kernel_only(args, wl):
@@ -415,6 +493,7 @@ def main():
     ap.add_argument("--workload", default="q1_256_adaptive")
     ap.add_argument("--no-arms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-layers", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--ref-samples", type=int, default=32)
     ap.add_argument("--kernel-only", action="store_true", help="time the ensemble SpMV alone (profiling)")

@@ -104,6 +104,14 @@ int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, const double 
                  const int32_t *rowptr, const int32_t *colidx, void *vals, int vals_f32,
                  double *dinv, double *b, void *stream);
 
+/* Parameter-based grouping indicator (Section 3.2, Eq. pb-indicator), the
+ * comparator of the surrogate grouping: for M samples xi[M][nparam] (device),
+ * H[m] = max over the points where the tensor is evaluated (FD face midpoints,
+ * Q1 element centroids) of lambda_max(A(x, xi_m)) / lambda_min(A(x, xi_m)).
+ * Sorting by H (ens_sort_chunk) gives the "par" grouping. */
+int ens_param_indicator(ens_handle h, const ens_problem *p, int M, const double *xi, double *H,
+                        void *stream);
+
 /* Bytes of caller workspace ens_pcg_solve needs (device memory, 256-byte aligned). */
 size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E);
 

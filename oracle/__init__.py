@@ -72,6 +72,8 @@ def _declare(L):
     L.or_pattern.argtypes = [c.c_int, c.c_int, _i64p, _i32p]
     L.or_assemble.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, _f64p, _i64p, _i32p, _f64p, _f64p]
     L.or_tensor.argtypes = [c.c_int, c.c_int, c.c_double, _f64p, _f64p, _f64p]
+    L.or_param_indicator.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, _f64p]
+    L.or_param_indicator.restype = c.c_double
     L.or_spmv.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, _f64p]
     L.or_spmv.restype = None
     L.or_jacobi.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p]
@@ -145,6 +147,11 @@ def tensor(kind: int, nparam: int, aniso: float, xi, x):
     if lib().or_tensor(kind, nparam, float(aniso), _f64(xi), _f64(x), K):
         raise ValueError("tensor failed")
     return K.reshape(d, d)
+
+
+def param_indicator(kind: int, n: int, nparam: int, aniso: float, xi) -> float:
+    """H(xi) = max over the evaluation points of lambda_max / lambda_min of A."""
+    return lib().or_param_indicator(kind, n, nparam, float(aniso), _f64(xi))
 
 
 # ---------------------------------------------------------------------------

@@ -53,6 +53,7 @@ int  or_assemble(int kind, int n, int nparam, double aniso, const double *xi,
  * manufactured-solution and eigenvalue checks through its effect only. */
 int  or_tensor(int kind, int nparam, double aniso, const double *xi,
                const double *x, double *K);
+double or_param_indicator(int kind, int n, int nparam, double aniso, const double *xi);
 
 /* ---- pcg.c -------------------------------------------------------------- */
 void or_spmv(int J, const int64_t *rowptr, const int32_t *colidx,

@@ -244,3 +244,55 @@ int or_assemble(int kind, int n, int nparam, double aniso, const double *xi,
         return assemble_q1(n, nparam, aniso, xi, rowptr, colidx, vals, b);
     return -1;
 }
+
+/* Parameter-based grouping indicator, Eq. (pb-indicator):
+ *   H(xi) = max over the points where the tensor is evaluated (FD face
+ *   midpoints, Q1 element centroids) of lambda_max(A) / lambda_min(A).
+ * Eigenvalues of the symmetric 2x2 / 3x3 tensor: 2x2 in closed form; the 3-D
+ * tensors of OR_FD7_AXIS are diagonal. */
+static double ratio2(const double *K)
+{
+    double t = 0.5 * (K[0] + K[3]);
+    double d = sqrt(0.25 * (K[0] - K[3]) * (K[0] - K[3]) + K[1] * K[2]);
+    return (t + d) / (t - d);
+}
+
+double or_param_indicator(int kind, int n, int nparam, double aniso, const double *xi)
+{
+    double K[9], x[3], H = 0.0;
+    if (kind == OR_Q1_ROT) {
+        for (int ey = 0; ey <= n; ey++)
+            for (int ex = 0; ex <= n; ex++) {
+                x[0] = coord((double)ex + 0.5, n);
+                x[1] = coord((double)ey + 0.5, n);
+                or_tensor(kind, nparam, aniso, xi, x, K);
+                double r = ratio2(K);
+                if (r > H) H = r;
+            }
+        return H;
+    }
+    int d = (kind == OR_FD7_AXIS) ? 3 : 2;
+    int J = (d == 3) ? n * n * n : n * n;
+    for (int p = 0; p < J; p++) {
+        int g[3] = {p % n, (p / n) % n, (d == 3) ? p / (n * n) : 0};
+        for (int axis = 0; axis < d; axis++)
+            for (int dir = -1; dir <= 1; dir += 2) {
+                for (int a = 0; a < d; a++) x[a] = coord((double)g[a] + 1.0, n);
+                x[axis] = coord((double)g[axis] + 1.0 + 0.5 * dir, n);
+                or_tensor(kind, nparam, aniso, xi, x, K);
+                double r;
+                if (d == 2) {
+                    r = ratio2(K);
+                } else {
+                    double mx = K[0], mn = K[0];
+                    if (K[4] > mx) mx = K[4];
+                    if (K[8] > mx) mx = K[8];
+                    if (K[4] < mn) mn = K[4];
+                    if (K[8] < mn) mn = K[8];
+                    r = mx / mn;
+                }
+                if (r > H) H = r;
+            }
+    }
+    return H;
+}

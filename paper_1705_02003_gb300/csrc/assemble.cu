@@ -252,6 +252,75 @@ __global__ void k_assemble_q1(int n, double aniso, int S, int E, const double *_
     }
 }
 
+// ---- parameter-based grouping indicator (Section 3.2, Eq. pb-indicator) -------
+// H(xi) = max over the points where the tensor is evaluated (FD face
+// midpoints, Q1 element centroids) of lambda_max(A) / lambda_min(A).  The
+// maximum of positive doubles is taken on their bit patterns with an integer
+// atomic, so the result does not depend on the order of the updates.
+__device__ __forceinline__ void hmax(double *H, double v)
+{
+    atomicMax(reinterpret_cast<unsigned long long *>(H), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_indicator(int kind, int n, int N, double aniso, int M, const double *__restrict__ xi_all,
+                            double *__restrict__ H)
+{
+    const int m = blockIdx.y;
+    const double *xs = xi_all + (size_t)m * N;
+    double x[8];
+    for (int k = 0; k < N; k++) x[k] = xs[k];
+    const double den = (double)(n + 1);
+    double best = 0.0;
+    if (kind == ENS_Q1_ROT) {
+        const int ne = (n + 1) * (n + 1);
+        const double th = dmul(0.25, dadd(1.0, x[2]));
+        const double c = cospi(th), sn = sinpi(th);
+        const double d2 = exp10(dmul(aniso, x[0]));
+        const double t11 = c * c + sn * sn * d2, t12 = c * sn * (1.0 - d2), t22 = sn * sn + c * c * d2;
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ne; q += gridDim.x * blockDim.x) {
+            const int ex = q % (n + 1), ey = q / (n + 1);
+            const double xc = ((double)ex + 0.5) / den, yc = ((double)ey + 0.5) / den;
+            const double sy = sinpi(yc);
+            const double a = exp(0.5 * (x[1] * (sinpi(xc) * sy) + x[3] * (sinpi(2.0 * xc) * sy) / 2.0));
+            const double k0 = a * t11, k1 = a * t12, k3 = a * t22;
+            const double t = 0.5 * (k0 + k3);
+            const double d = sqrt(0.25 * (k0 - k3) * (k0 - k3) + k1 * k1);
+            best = fmax(best, (t + d) / (t - d));
+        }
+    } else {
+        const int d = kind == ENS_FD7_AXIS ? 3 : 2;
+        const int J = d == 3 ? n * n * n : n * n;
+        const double d2 = exp10(aniso * x[0]);
+        const double d3 = d == 3 ? exp10(aniso * x[1]) : 1.0;
+        for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < J; p += gridDim.x * blockDim.x) {
+            const int g[3] = {p % n, (p / n) % n, d == 3 ? p / (n * n) : 0};
+            for (int axis = 0; axis < d; axis++)
+                for (int dir = -1; dir <= 1; dir += 2) {
+                    double c[3];
+                    for (int q = 0; q < d; q++) c[q] = (double)(g[q] + 1) / den;
+                    c[axis] = ((double)(g[axis] + 1) + 0.5 * dir) / den;
+                    double e = d == 3 ? fd7_e(x, c[0], c[1], c[2]) : fd5_a(x, N, c[0], c[1]);
+                    double kx = e, ky = e * d2, kz = e * d3;
+                    double mx = fmax(kx, ky), mn = fmin(kx, ky);
+                    if (d == 3) {
+                        mx = fmax(mx, kz);
+                        mn = fmin(mn, kz);
+                    }
+                    best = fmax(best, mx / mn);
+                }
+        }
+    }
+    // block maximum, then one atomic per block
+    __shared__ double sh[256];
+    sh[threadIdx.x] = best;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + off]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) hmax(H + m, sh[0]);
+}
+
 unsigned grid_for(long long total, int block)
 {
     long long g = (total + block - 1) / block;
@@ -361,5 +430,28 @@ extern "C" int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, co
         break;
     }
     ENS_LAUNCH_CHECK(h, "ens_assemble: kernel launch");
+    return ENS_OK;
+}
+
+extern "C" int ens_param_indicator(ens_handle h, const ens_problem *p, int M, const double *xi, double *H,
+                                   void *stream)
+{
+    if (!h) return ENS_EINVAL;
+    int J;
+    int64_t nnz;
+    std::string why;
+    int rc = problem_check(p, &J, &nnz, &why);
+    if (rc) return set_error(h, rc, "ens_param_indicator: " + why);
+    if (M < 0 || M > 65535) return set_error(h, ENS_EINVAL, "ens_param_indicator: M must be in 0..65535");
+    if (M == 0) return ENS_OK;
+    if (!xi || !H) return set_error(h, ENS_EINVAL, "ens_param_indicator: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(H, 0, (size_t)M * sizeof(double), st));
+    const long long pts = p->kind == ENS_Q1_ROT ? (long long)(p->n + 1) * (p->n + 1) : (long long)J;
+    unsigned bx = (unsigned)((pts + 255) / 256);
+    if (bx > 64) bx = 64;
+    dim3 grid(bx, M);
+    k_indicator<<<grid, 256, 0, st>>>(p->kind, p->n, p->nparam, p->aniso, M, xi, H);
+    ENS_LAUNCH_CHECK(h, "ens_param_indicator");
     return ENS_OK;
 }

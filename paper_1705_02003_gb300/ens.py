@@ -25,7 +25,7 @@ EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "e
            "ens_assemble", "ens_pcg_workspace_size", "ens_pcg_solve", "ens_group", "ens_sort_chunk",
            "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv",
            "ens_pcg_solve_static", "ens_pcg_ir_workspace_size", "ens_pcg_solve_ir",
-           "ens_adjoint_workspace_size", "ens_adjoint_grad")
+           "ens_adjoint_workspace_size", "ens_adjoint_grad", "ens_param_indicator")
 
 _lib = None
 _lock = threading.Lock()
@@ -78,6 +78,7 @@ def _declare(L):
     L.ens_sg_eval.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_int, vp, vp, vp, vp]
     L.ens_qoi.argtypes = [vp, c.c_int, c.c_int, c.c_int, vp, vp, vp, vp]
     L.ens_spmv.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_param_indicator.argtypes = [vp, c.POINTER(Problem), c.c_int, vp, vp, vp]
     L.ens_adjoint_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
     L.ens_adjoint_workspace_size.restype = c.c_size_t
     L.ens_adjoint_grad.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
@@ -252,6 +253,17 @@ def ens_pcg_solve_ir(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx
                                  _ptr(outer_its), _ptr(relres), _ptr(status), _ptr(work), work.numel(),
                                  _stream(stream))
     h.check(rc, "ens_pcg_solve_ir")
+
+
+def ens_param_indicator(h: Handle, prob: Problem, xi, H, stream=None):
+    """H[m] = max_x lambda_max / lambda_min of A(x, xi_m) (the "par" grouping key)."""
+    _check_dtype(xi, torch.float64, "xi")
+    _check_dtype(H, torch.float64, "H")
+    M = H.numel()
+    if xi.numel() != M * prob.nparam:
+        raise ValueError("xi must be [M][nparam]")
+    rc = load().ens_param_indicator(h.ptr, ctypes.byref(prob), int(M), _ptr(xi), _ptr(H), _stream(stream))
+    h.check(rc, "ens_param_indicator")
 
 
 def ens_adjoint_workspace_size(prob: Problem, S: int, E: int) -> int:

@@ -9,9 +9,10 @@ steps 1-4 of the flowchart) on the GPU path.
          stop when nothing is refined or |Y| + |Y_new| > n_max
       4. group the new points by the iteration surrogate (ens_group) and go to 1.
 
-Groupings: "sur" (the surrogate, Section 3.1), "nat" (generation order), "rand"
-(a seeded permutation), all with S-sample ensembles; "its" (sorted by the
-actual counts, known only afterwards) is reported through R only.
+Groupings: "sur" (the surrogate, Section 3.1), "par" (the anisotropy indicator
+of Section 3.2), "nat" (generation order), "rand" (a seeded permutation), all
+with S-sample ensembles; "its" (sorted by the actual counts, known only
+afterwards) is reported through R only.
 
 The grid table (levels, indices, surpluses) stays on the device in generation
 order; per level the host reads back only the G surpluses it refines on.
@@ -134,6 +135,12 @@ class Adaptive:
                 perm = torch.empty(Mn, dtype=torch.int32, device=dev)
                 ens.ens_group(self.h, lvl_d, idx_d, cI, yn, S, pred, perm)
                 self.launches += 2
+            elif grouping == "par":
+                # parameter-based grouping (Section 3.2): sort by the anisotropy indicator H
+                perm = torch.empty(Mn, dtype=torch.int32, device=dev)
+                ens.ens_param_indicator(self.h, self.prob, yn, pred)
+                ens.ens_sort_chunk(self.h, pred, S, perm)
+                self.launches += 2
             elif grouping == "nat":
                 perm = torch.arange(Mn, dtype=torch.int32, device=dev)
             elif grouping == "rand":
@@ -150,7 +157,7 @@ class Adaptive:
             first = len(lvl)
             levels.append((first, first + Mn))
             perms.append(perm.cpu().numpy())
-            preds.append(pred.cpu().numpy() if grouping == "sur" else np.zeros(Mn))
+            preds.append(pred.cpu().numpy() if grouping in ("sur", "par") else np.zeros(Mn))
             lvl = np.concatenate([lvl, nl])
             idx = np.concatenate([idx, ni])
             lvl_d = torch.cat([lvl_d, torch.from_numpy(nl).to(dev)])

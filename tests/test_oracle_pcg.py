@@ -362,3 +362,19 @@ def test_batch_equals_individual_and_is_order_free():
         np.testing.assert_array_equal(x, out["x"][m])
         assert it == out["iters"][m]
         assert out["G"][m] == pytest.approx(float(x @ x), rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# parameter-based grouping indicator: closed forms of the eigenvalue ratio
+# ---------------------------------------------------------------------------
+def test_param_indicator_closed_forms():
+    rng = np.random.default_rng(13)
+    for _ in range(5):
+        xi = rng.uniform(-1, 1, 8)
+        # 2-D fields: a scalar field times diag(1, d) (or a rotation of it): ratio 10^(aniso |xi_1|)
+        assert O.param_indicator(O.FD5_LOGKL, 9, 8, 3.0, xi) == pytest.approx(10 ** (3 * abs(xi[0])), rel=1e-12)
+        assert O.param_indicator(O.Q1_ROT, 9, 4, 4.0, xi[:4]) == pytest.approx(10 ** (4 * abs(xi[0])), rel=1e-10)
+        # 3-D: diag(1, 10^(a xi_1), 10^(a xi_2)) times a scalar
+        e = np.array([0.0, xi[0], xi[1]])
+        want = 10 ** (2.0 * (e.max() - e.min()))
+        assert O.param_indicator(O.FD7_AXIS, 5, 6, 2.0, xi[:6]) == pytest.approx(want, rel=1e-12)

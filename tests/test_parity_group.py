@@ -142,3 +142,37 @@ def test_adaptive_loop_matches_oracle(h, small_run):
         np.testing.assert_allclose(R["run"][0], Ro["sur"][0], rtol=1e-12)
     for lev, (a, b) in enumerate(run["levels"]):
         assert R["run"][0][lev] >= 1.0
+
+
+@pytest.mark.parametrize("kind,n,N,aniso", [("fd5", 32, 2, 3.0), ("q1", 64, 4, 4.0), ("fd7", 12, 6, 2.0),
+                                            ("fd5", 40, 8, 3.0)])
+def test_param_indicator_matches_oracle(h, kind, n, N, aniso):
+    from gpu_util import OKIND
+
+    M = 37
+    xi = inputs.draws(M, N, seed=70 + n)
+    xi[:8] = np.round(xi[:8] * 4) / 4  # dyadic points, as on a sparse grid: many equal indicators
+    H = torch.empty(M, dtype=torch.float64, device="cuda")
+    ens.ens_param_indicator(h, ens.problem(kind, n, N, aniso), dev(xi), H)
+    Hg = H.cpu().numpy()
+    Ho = np.array([O.param_indicator(OKIND[kind], n, N, aniso, xi[m]) for m in range(M)])
+    np.testing.assert_allclose(Hg, Ho, rtol=1e-12)
+    perm = torch.empty(M, dtype=torch.int32, device="cuda")
+    ens.ens_sort_chunk(h, H, 8, perm)
+    # a stable ascending sort of the GPU keys (Python's sort is stable)
+    assert perm.cpu().numpy().tolist() == sorted(range(M), key=lambda i: Hg[i])
+
+
+def test_parameter_grouping_in_the_loop(h):
+    """The loop with "par" grouping visits the same grid (grouping never
+    changes the grid) and its R is at least the iteration-sorted R on full
+    levels."""
+    wl = inputs.WORKLOADS["fd5_32_adaptive"]
+    ad = uq.Adaptive(h, wl)
+    sur = ad.run("sur")
+    par = ad.run("par")
+    assert np.array_equal(sur["lvl"], par["lvl"]) and np.array_equal(sur["I"], par["I"])
+    R = uq.ratios(par)
+    for lev, (a, b) in enumerate(par["levels"]):
+        if (b - a) % wl.S == 0:
+            assert R["its"][0][lev] <= R["run"][0][lev] + 1e-12

@@ -138,6 +138,28 @@ int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   double rtol, int maxit, int32_t *iters, double *relres, int32_t *status,
                   void *work, size_t work_bytes, void *stream);
 
+/* Bytes of caller workspace ens_solve_stream needs (0 for bad arguments). */
+size_t ens_stream_workspace_size(const ens_problem *p, int S, int E);
+
+/* Continuous ensemble batching (the batching layer; the paper solves fixed
+ * ensembles one after another, Section 4).  M samples xi[M][nparam] (device)
+ * run through a pool of E ensembles of S lanes, in the queue order order[M]
+ * (device int32 permutation; NULL = 0, 1, ...).  The device while loop runs
+ * `chunk` trips at a time; after each chunk every lane that has frozen
+ * (converged, maxit, breakdown) returns its outcome by sample index and takes
+ * the next queued sample: only that lane's values are assembled and only its
+ * CG state restarts, while the other lanes keep iterating.  When the queue is
+ * empty the live lanes are re-packed into as few ensembles as hold them.
+ * Each sample's iteration and result are those of ens_pcg_solve for it.
+ * Outputs by sample: iters[M], status[M], relres[M], and qoi[M] (may be NULL)
+ * = ||u||_2^2, or w^T u when w[J] (device) is given.  The graph, values,
+ * vectors and lane state live in the caller's workspace
+ * (ens_stream_workspace_size).  Synchronises `stream` once per chunk. */
+int ens_solve_stream(ens_handle h, const ens_problem *p, int S, int E, int M, const double *xi,
+                     const int32_t *order, const double *w, double rtol, int maxit, int chunk,
+                     int32_t *iters, int32_t *status, double *relres, double *qoi, void *work,
+                     size_t work_bytes, void *stream);
+
 /* Bytes of caller workspace ens_adjoint_grad needs (0 for bad arguments). */
 size_t ens_adjoint_workspace_size(const ens_problem *p, int S, int E);
 

@@ -94,7 +94,7 @@ __device__ __forceinline__ void put(V *vals, long long idx, double v) { vals[idx
 template <typename V>
 __global__ void k_assemble_fd5(int n, int N, double aniso, int S, int E, const double *__restrict__ xi,
                                const int32_t *__restrict__ rowptr, V *__restrict__ vals,
-                               double *__restrict__ dinv, double *__restrict__ b, long long nnz)
+                               double *__restrict__ dinv, double *__restrict__ b, long long nnz, const uint8_t *__restrict__ lane_mask)
 {
     const int J = n * n;
     const long long total = (long long)E * J * S;
@@ -106,6 +106,7 @@ __global__ void k_assemble_fd5(int n, int N, double aniso, int S, int E, const d
         long long er = t / S;
         int row = (int)(er % J);
         int e = (int)(er / J);
+        if (lane_mask && !lane_mask[e * S + s]) continue;
         double x[8];
         const double *xs = xi + ((long long)e * S + s) * N;
         for (int k = 0; k < N; k++) x[k] = xs[k];
@@ -135,7 +136,7 @@ __global__ void k_assemble_fd5(int n, int N, double aniso, int S, int E, const d
 template <typename V>
 __global__ void k_assemble_fd7(int n, double aniso, int S, int E, const double *__restrict__ xi,
                                const int32_t *__restrict__ rowptr, V *__restrict__ vals,
-                               double *__restrict__ dinv, double *__restrict__ b, long long nnz)
+                               double *__restrict__ dinv, double *__restrict__ b, long long nnz, const uint8_t *__restrict__ lane_mask)
 {
     const int n2 = n * n;
     const int J = n2 * n;
@@ -148,6 +149,7 @@ __global__ void k_assemble_fd7(int n, double aniso, int S, int E, const double *
         long long er = t / S;
         int row = (int)(er % J);
         int e = (int)(er / J);
+        if (lane_mask && !lane_mask[e * S + s]) continue;
         double x[6];
         const double *xs = xi + ((long long)e * S + s) * 6;
         for (int k = 0; k < 6; k++) x[k] = xs[k];
@@ -187,7 +189,7 @@ __device__ __forceinline__ double q1_sign(int u) { return u ? 1.0 : -1.0; }
 template <typename V>
 __global__ void k_assemble_q1(int n, double aniso, int S, int E, const double *__restrict__ xi,
                               const int32_t *__restrict__ rowptr, V *__restrict__ vals,
-                              double *__restrict__ dinv, double *__restrict__ b, long long nnz)
+                              double *__restrict__ dinv, double *__restrict__ b, long long nnz, const uint8_t *__restrict__ lane_mask)
 {
     const int J = n * n;
     const long long total = (long long)E * J * S;
@@ -198,6 +200,7 @@ __global__ void k_assemble_q1(int n, double aniso, int S, int E, const double *_
         long long er = t / S;
         int row = (int)(er % J);
         int e = (int)(er / J);
+        if (lane_mask && !lane_mask[e * S + s]) continue;
         const double *xs = xi + ((long long)e * S + s) * 4;
         double x0 = xs[0], x1 = xs[1], x2 = xs[2], x3 = xs[3];
         int i = row % n, j = row / n;
@@ -391,6 +394,56 @@ extern "C" int ens_pattern(ens_handle h, const ens_problem *p, int32_t *rowptr, 
     return ENS_OK;
 }
 
+namespace ens {
+int assemble_lanes(ens_ctx *h, const ens_problem *p, int S, int E, const double *xi, const int32_t *rowptr,
+                   void *vals, int vals_f32, double *dinv, double *b, const uint8_t *lane_mask, cudaStream_t st)
+{
+    int J;
+    int64_t nnz;
+    std::string why;
+    int rc = problem_check(p, &J, &nnz, &why);
+    if (rc) return set_error(h, rc, "ens_assemble: " + why);
+    long long total = (long long)E * J * S;
+    unsigned grid = grid_for(total, 256);
+    switch (p->kind) {
+    case ENS_FD5_LOGKL:
+        if (vals_f32)
+            k_assemble_fd5<float><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lane_mask);
+        else
+            k_assemble_fd5<double><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lane_mask);
+        break;
+    case ENS_Q1_ROT:
+        if (vals_f32)
+            k_assemble_q1<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lane_mask);
+        else
+            k_assemble_q1<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lane_mask);
+        break;
+    default:
+        if (vals_f32)
+            k_assemble_fd7<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lane_mask);
+        else
+            k_assemble_fd7<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lane_mask);
+        break;
+    }
+    ENS_LAUNCH_CHECK(h, "ens_assemble: kernel launch");
+    return ENS_OK;
+}
+
+int pattern_into(ens_ctx *h, const ens_problem *p, int32_t *rowptr, int32_t *colidx, cudaStream_t st)
+{
+    int J;
+    int64_t nnz;
+    std::string why;
+    int rc = problem_check(p, &J, &nnz, &why);
+    if (rc) return set_error(h, rc, "pattern: " + why);
+    k_rowptr<<<1, 1024, 0, st>>>(p->kind, p->n, J, rowptr);
+    ENS_LAUNCH_CHECK(h, "pattern: rowptr kernel");
+    k_colidx<<<(J + 255) / 256, 256, 0, st>>>(p->kind, p->n, J, rowptr, colidx);
+    ENS_LAUNCH_CHECK(h, "pattern: colidx kernel");
+    return ENS_OK;
+}
+}  // namespace ens
+
 extern "C" int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, const double *xi,
                             const int32_t *rowptr, const int32_t *colidx, void *vals, int vals_f32,
                             double *dinv, double *b, void *stream)
@@ -405,32 +458,7 @@ extern "C" int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, co
     if (E < 0) return set_error(h, ENS_EINVAL, "ens_assemble: E < 0");
     if (E == 0) return ENS_OK;
     if (!xi || !rowptr || !colidx || !vals) return set_error(h, ENS_EINVAL, "ens_assemble: null pointer");
-    (void)colidx;
-    cudaStream_t st = (cudaStream_t)stream;
-    long long total = (long long)E * J * S;
-    unsigned grid = grid_for(total, 256);
-    switch (p->kind) {
-    case ENS_FD5_LOGKL:
-        if (vals_f32)
-            k_assemble_fd5<float><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz);
-        else
-            k_assemble_fd5<double><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz);
-        break;
-    case ENS_Q1_ROT:
-        if (vals_f32)
-            k_assemble_q1<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz);
-        else
-            k_assemble_q1<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz);
-        break;
-    default:
-        if (vals_f32)
-            k_assemble_fd7<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz);
-        else
-            k_assemble_fd7<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz);
-        break;
-    }
-    ENS_LAUNCH_CHECK(h, "ens_assemble: kernel launch");
-    return ENS_OK;
+    return assemble_lanes(h, p, S, E, xi, rowptr, vals, vals_f32, dinv, b, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int ens_param_indicator(ens_handle h, const ens_problem *p, int M, const double *xi, double *H,

@@ -71,6 +71,8 @@ struct Args {
     Ws w;
     double *pq_out;  // ens_spmv: write p^T q per lane here instead of alpha
     int in_graph;    // K4 drives the graph's while loop (else the host loops)
+    int trip_cap;    // trips per launch of the loop (maxit, or the chunk of a streamed solve)
+    const uint8_t *refill;  // K0: restart only these lanes, keep the others (NULL: all lanes)
     cudaGraphConditionalHandle cond;
 };
 
@@ -285,12 +287,25 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restric
     const size_t vbase = (size_t)e * a.J * S;
     double acc[2][V] = {};
     const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
-    for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
+    bool rf[V], any = false, all = true;
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        rf[v] = a.refill ? a.refill[e * S + lane0 + v] != 0 : true;
+        any = any || rf[v];
+        all = all && rf[v];
+    }
+    for (int r = r0 + threadIdx.x / TPR; any && r < r1; r += RPP) {
         size_t o = vbase + (size_t)r * S + lane0;
         Vec<T, V> dv, xv, rv, pv;
         dv.load_ro(dinv + o);
+        if (!all) {  // lanes that keep running share this access: keep their values
+            xv.load(xx + o);
+            rv.load(rr + o);
+            pv.load(pp + o);
+        }
 #pragma unroll
         for (int v = 0; v < V; v++) {
+            if (!rf[v]) continue;
             xv.v[v] = T(0);
             rv.v[v] = (T)__ldg(bb + o + v);
             pv.v[v] = dv.v[v] * rv.v[v];
@@ -306,7 +321,7 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restric
     if (threadIdx.x == 0) live_cnt = 0;
     double *parts[2] = {a.w.part0, a.w.part1};
     if (!reduce_lanes<LG, S, 2>(acc, parts, e, a.g.nblk, a.w.counter + e * CNT_KINDS + CNT_INIT, tot)) return;
-    if (threadIdx.x < S) {
+    if (threadIdx.x < S && (!a.refill || a.refill[e * S + threadIdx.x])) {
         const int s = threadIdx.x, L = e * S + s;
         const double bsq = tot[s], rz = tot[S + s];
         const int act = a.active ? (int)a.active[L] : 1;
@@ -334,7 +349,10 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restric
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        a.w.ens_live[e] = live_cnt;
+        if (a.refill)
+            a.w.ens_live[e] += live_cnt;
+        else
+            a.w.ens_live[e] = live_cnt;
         atomicAdd(a.w.ctl + CTL_NLIVE, live_cnt);
     }
 }
@@ -509,7 +527,7 @@ __global__ void __launch_bounds__(kBlock) k_direction(Args a, const T *__restric
         // K3 has finished for every ensemble, so the live count is final here.
         const int trips = a.w.ctl[CTL_TRIPS] + 1;
         a.w.ctl[CTL_TRIPS] = trips;
-        const int more = (a.w.ctl[CTL_NLIVE] > 0) && (trips < a.maxit);
+        const int more = (a.w.ctl[CTL_NLIVE] > 0) && (trips < a.trip_cap);
         if (a.in_graph) cudaGraphSetConditional(a.cond, more ? 1u : 0u);
     }
     if (a.w.ens_live[e] == 0) return;
@@ -616,7 +634,7 @@ int loop_graph(ens_ctx *h, Args a, cudaGraphExec_t *out)
                                  bits(a.x), bits(a.active), bits(a.iters), bits(a.status), bits(a.relres),
                                  bits(a.w.r), bits(a.w.part0), bits(a.w.live), (uint64_t)a.J, (uint64_t)a.S,
                                  (uint64_t)a.E, (uint64_t)a.maxit, (uint64_t)a.nnz, bits(a.rtol),
-                                 (uint64_t)a.g.nblk, (uint64_t)a.g.RT, (uint64_t)sizeof(T)};
+                                 (uint64_t)a.g.nblk, (uint64_t)a.g.RT, (uint64_t)sizeof(T), (uint64_t)a.trip_cap};
     h->clock++;
     for (auto &ge : h->graphs)
         if (ge.key == key) {
@@ -696,7 +714,7 @@ int run_solve(ens_ctx *h, const Args &a, cudaStream_t st, bool host_loop)
         // every 16 trips (profilers see each launch; the graph path does not
         // expose kernels inside a conditional body to them).
         int ctl[2] = {1, 0};
-        while (ctl[0] > 0 && ctl[1] < a.maxit) {
+        while (ctl[0] > 0 && ctl[1] < a.trip_cap) {
             for (int t = 0; t < 16; t++) dispatch_body<T>(a, st);
             ENS_LAUNCH_CHECK(h, "PCG loop kernels");
             ENS_CUDA_CHECK(h, cudaMemcpyAsync(ctl, a.w.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
@@ -757,6 +775,7 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
     a.J = J; a.S = S; a.E = E; a.maxit = maxit; a.nnz = nnz; a.rtol = rtol; a.g = g;
     a.rowptr = rowptr; a.colidx = colidx; a.vals = vals; a.dinv = dinv; a.b = b; a.x = x;
     a.active = active; a.iters = iters; a.status = status; a.relres = relres;
+    a.trip_cap = maxit;
     layout(J, S, E, g, &a.w, (char *)work);
     return run_solve<double>(h, a, (cudaStream_t)stream, h->host_loop != 0);
 }
@@ -1017,7 +1036,7 @@ extern "C" int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E, 
     sa.J = J; sa.S = S; sa.E = E; sa.maxit = maxit_inner; sa.nnz = nnz; sa.rtol = rtol_inner; sa.g = g;
     sa.rowptr = rowptr; sa.colidx = colidx; sa.vals = vals32; sa.dinv = ia.w.dinv32; sa.b = ia.w.r64;
     sa.x = ia.w.d32; sa.active = ia.w.iactive; sa.iters = ia.w.iiters; sa.status = ia.w.istatus;
-    sa.relres = ia.w.irelres; sa.w = ia.w.inner;
+    sa.relres = ia.w.irelres; sa.w = ia.w.inner; sa.trip_cap = maxit_inner;
     ENS_CUDA_CHECK(h, cudaMemsetAsync(sa.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
     k_ir_prep<<<152 * 4, 256, 0, st>>>(ia, dinv, x);
     ENS_LAUNCH_CHECK(h, "ens_pcg_solve_ir: prep");
@@ -1050,6 +1069,319 @@ extern "C" int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E, 
         }
         k_ir_lanes<<<(E * S + 255) / 256, 256, 0, st>>>(ia);
         ENS_LAUNCH_CHECK(h, "ens_pcg_solve_ir: update");
+    }
+    return ENS_OK;
+}
+
+// ---- continuous ensemble batching (the batching layer) ---------------------------
+// M samples run through a pool of E ensembles of S lanes.  The device loop runs
+// a chunk of trips; then every lane that froze gives its outcome back (by
+// sample index) and takes the next queued sample: its values are assembled
+// into that lane alone and its CG state restarts, while the other lanes keep
+// iterating.  Once the queue is empty, the live lanes are re-packed into as
+// few ensembles as hold them, so drained ensembles cost nothing.
+namespace ens {
+namespace {
+
+struct StreamWs {
+    int32_t *rowptr, *colidx;
+    double *vals, *dinv, *b, *x;  // [E][nnz][S], [E][J][S]
+    double *lane_xi;              // [E][S][N]
+    int32_t *lane_sample;         // [E][S], -1 = empty
+    int32_t *lane_iters, *lane_status;
+    double *lane_relres;
+    uint8_t *active, *refill;     // [E][S]
+    int32_t *list;                // [2 E S] harvest lanes / re-pack moves
+    Ws loop;
+};
+
+size_t stream_layout(int J, int64_t nnz, int S, int E, int N, const Geo &g, StreamWs *w, char *base)
+{
+    Bump m(base);
+    StreamWs t;
+    const size_t lanes = (size_t)E * S;
+    t.rowptr = (int32_t *)m.take((size_t)(J + 1) * 4);
+    t.colidx = (int32_t *)m.take((size_t)nnz * 4);
+    t.vals = (double *)m.take((size_t)E * nnz * S * 8);
+    t.dinv = (double *)m.take((size_t)E * J * S * 8);
+    t.b = (double *)m.take((size_t)E * J * S * 8);
+    t.x = (double *)m.take((size_t)E * J * S * 8);
+    t.lane_xi = (double *)m.take(lanes * N * 8);
+    t.lane_sample = (int32_t *)m.take(lanes * 4);
+    t.lane_iters = (int32_t *)m.take(lanes * 4);
+    t.lane_status = (int32_t *)m.take(lanes * 4);
+    t.lane_relres = (double *)m.take(lanes * 8);
+    t.active = (uint8_t *)m.take(lanes);
+    t.refill = (uint8_t *)m.take(lanes);
+    t.list = (int32_t *)m.take(lanes * 2 * 4);
+    lay_loop(m, J, S, E, g, sizeof(double), &t.loop);
+    if (w) *w = t;
+    return m.off;
+}
+
+// lane_xi of the refilled lanes from the caller's samples.
+__global__ void k_gather_xi(int lanes, int N, const uint8_t *__restrict__ refill, const int32_t *__restrict__ sample,
+                            const double *__restrict__ xi, double *__restrict__ lane_xi)
+{
+    int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= lanes || !refill[L] || sample[L] < 0) return;
+    for (int k = 0; k < N; k++) lane_xi[(size_t)L * N + k] = xi[(size_t)sample[L] * N + k];
+}
+
+// Outcome of finished lanes (list of lane ids) to their samples; QoI by one
+// block per lane (fixed order: thread t sums rows t, t + 256, ..., then a tree).
+__global__ void k_harvest(int nh, const int32_t *__restrict__ list, int J, int S, const int32_t *__restrict__ sample,
+                          const double *__restrict__ x, const double *__restrict__ w,
+                          const int32_t *__restrict__ lane_iters, const int32_t *__restrict__ lane_status,
+                          const double *__restrict__ lane_relres, int32_t *iters, int32_t *status, double *relres,
+                          double *qoi)
+{
+    __shared__ double sh[256];
+    if ((int)blockIdx.x >= nh) return;
+    const int L = list[blockIdx.x];
+    const int e = L / S, s = L % S;
+    const double *xe = x + (size_t)e * J * S + s;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) {
+        const double v = xe[(size_t)j * S];
+        acc = fma(w ? w[j] : v, v, acc);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) sh[threadIdx.x] = dadd(sh[threadIdx.x], sh[threadIdx.x + off]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int m = sample[L];
+        iters[m] = lane_iters[L];
+        status[m] = lane_status[L];
+        relres[m] = lane_relres[L];
+        if (qoi) qoi[m] = sh[0];
+    }
+}
+
+// Re-pack: move live lanes (list of (src, dst) pairs) -- their values, vectors
+// and CG state -- so the drained ensembles go idle.  Grid: (chunks, moves).
+__global__ void k_repack(int nm, const int32_t *__restrict__ moves, int J, long long nnz, int S, int N,
+                         StreamWs w)
+{
+    const int mv = blockIdx.y;
+    if (mv >= nm) return;
+    const int src = moves[2 * mv], dst = moves[2 * mv + 1];
+    const int es = src / S, ss = src % S, ed = dst / S, sd = dst % S;
+    const size_t vs = (size_t)es * nnz * S + ss, vd = (size_t)ed * nnz * S + sd;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
+        w.vals[vd + (size_t)k * S] = w.vals[vs + (size_t)k * S];
+    const size_t xs = (size_t)es * J * S + ss, xd = (size_t)ed * J * S + sd;
+    double *r = (double *)w.loop.r, *p = (double *)w.loop.p;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < J; j += (long long)gridDim.x * blockDim.x) {
+        const size_t a = xs + (size_t)j * S, c = xd + (size_t)j * S;
+        w.x[c] = w.x[a];
+        w.dinv[c] = w.dinv[a];
+        w.b[c] = w.b[a];
+        r[c] = r[a];
+        p[c] = p[a];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        w.loop.bnorm[dst] = w.loop.bnorm[src];
+        w.loop.rz[dst] = w.loop.rz[src];
+        w.loop.rr[dst] = w.loop.rr[src];
+        w.loop.k[dst] = w.loop.k[src];
+        w.loop.live[dst] = w.loop.live[src];
+        w.loop.live[src] = 0;
+        w.lane_sample[dst] = w.lane_sample[src];
+        w.lane_sample[src] = -1;
+        w.lane_status[dst] = w.lane_status[src];
+        w.lane_iters[dst] = w.lane_iters[src];
+        w.lane_relres[dst] = w.lane_relres[src];
+        for (int k = 0; k < N; k++) w.lane_xi[(size_t)dst * N + k] = w.lane_xi[(size_t)src * N + k];
+    }
+}
+
+__global__ void k_count_live(int E, int S, const int *__restrict__ live, int *__restrict__ ens_live)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int c = 0;
+    for (int s = 0; s < S; s++) c += live[e * S + s];
+    ens_live[e] = c;
+}
+
+}  // namespace
+}  // namespace ens
+
+extern "C" size_t ens_stream_workspace_size(const ens_problem *p, int S, int E)
+{
+    int J;
+    int64_t nnz;
+    std::string why;
+    if (problem_check(p, &J, &nnz, &why) || !lane_count_ok(S) || E <= 0) return 0;
+    return stream_layout(J, nnz, S, E, p->nparam, geometry(J, S), nullptr, nullptr);
+}
+
+extern "C" int ens_solve_stream(ens_handle h, const ens_problem *p, int S, int E, int M, const double *xi,
+                                const int32_t *order, const double *w, double rtol, int maxit, int chunk,
+                                int32_t *iters, int32_t *status, double *relres, double *qoi, void *work,
+                                size_t work_bytes, void *stream)
+{
+    if (!h) return ENS_EINVAL;
+    int J;
+    int64_t nnz;
+    std::string why;
+    int rc = problem_check(p, &J, &nnz, &why);
+    if (rc) return set_error(h, rc, "ens_solve_stream: " + why);
+    rc = check_solve_args(h, "ens_solve_stream", J, nnz, S, E, rtol, maxit);
+    if (rc) return rc;
+    if (E < 1 || M < 0 || chunk < 1) return set_error(h, ENS_EINVAL, "ens_solve_stream: need E >= 1, M >= 0, chunk >= 1");
+    if (M == 0) return ENS_OK;
+    if (!xi || !iters || !status || !relres || !work) return set_error(h, ENS_EINVAL, "ens_solve_stream: null pointer");
+    Geo g = geometry(J, S);
+    const size_t need = stream_layout(J, nnz, S, E, p->nparam, g, nullptr, nullptr);
+    if (work_bytes < need)
+        return set_error(h, ENS_ENOMEM, "ens_solve_stream: workspace too small (need " + std::to_string(need) + " bytes)");
+    cudaStream_t st = (cudaStream_t)stream;
+    StreamWs sw;
+    stream_layout(J, nnz, S, E, p->nparam, g, &sw, (char *)work);
+    const int N = p->nparam, lanes = E * S;
+    rc = pattern_into(h, p, sw.rowptr, sw.colidx, st);
+    if (rc) return rc;
+
+    // the queue, in the caller's order
+    std::vector<int32_t> queue(M);
+    if (order) {
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(queue.data(), order, (size_t)M * 4, cudaMemcpyDeviceToHost, st));
+        ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+        std::vector<char> seen(M, 0);
+        for (int i = 0; i < M; i++) {
+            if (queue[i] < 0 || queue[i] >= M || seen[queue[i]])
+                return set_error(h, ENS_EINVAL, "ens_solve_stream: order is not a permutation of 0..M-1");
+            seen[queue[i]] = 1;
+        }
+    } else {
+        for (int i = 0; i < M; i++) queue[i] = i;
+    }
+    int next = 0;
+    std::vector<int32_t> lane_sample(lanes, -1);
+    std::vector<uint8_t> refill(lanes, 0);
+    std::vector<int> live(lanes, 0);
+    std::vector<int32_t> list;
+
+    Args a;
+    memset(&a, 0, sizeof(a));
+    a.J = J; a.S = S; a.E = E; a.maxit = maxit; a.nnz = nnz; a.rtol = rtol; a.g = g;
+    a.rowptr = sw.rowptr; a.colidx = sw.colidx; a.vals = sw.vals; a.dinv = sw.dinv; a.b = sw.b; a.x = sw.x;
+    a.active = sw.active; a.iters = sw.lane_iters; a.status = sw.lane_status; a.relres = sw.lane_relres;
+    a.w = sw.loop;
+    a.trip_cap = chunk;
+
+    // first fill: every lane gets a sample while the queue lasts; empty lanes
+    // carry a copy of sample queue[0] so their (unused) values stay finite
+    for (int L = 0; L < lanes; L++) {
+        if (next < M) lane_sample[L] = queue[next++];
+        refill[L] = 1;
+    }
+    {
+        std::vector<int32_t> fill_sample(lane_sample);
+        std::vector<uint8_t> act(lanes);
+        for (int L = 0; L < lanes; L++) {
+            act[L] = lane_sample[L] >= 0;
+            if (fill_sample[L] < 0) fill_sample[L] = queue[0];
+        }
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.lane_sample, fill_sample.data(), lanes * 4, cudaMemcpyHostToDevice, st));
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.refill, refill.data(), lanes, cudaMemcpyHostToDevice, st));
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.active, act.data(), lanes, cudaMemcpyHostToDevice, st));
+        k_gather_xi<<<(lanes + 255) / 256, 256, 0, st>>>(lanes, N, sw.refill, sw.lane_sample, xi, sw.lane_xi);
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.lane_sample, lane_sample.data(), lanes * 4, cudaMemcpyHostToDevice, st));
+        rc = assemble_lanes(h, p, S, E, sw.lane_xi, sw.rowptr, sw.vals, 0, sw.dinv, sw.b, nullptr, st);
+        if (rc) return rc;
+        ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
+        ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl, 0, 2 * sizeof(int), st));
+        dispatch_init<double>(a, st);
+        ENS_LAUNCH_CHECK(h, "ens_solve_stream: first fill");
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (!h->host_loop) {
+        rc = loop_graph<double>(h, a, &exec);
+        if (rc) return rc;
+    }
+    bool repacked_all = false;
+    const long long max_rounds = ((long long)M / lanes + 2) * ((long long)maxit / chunk + 2) + 16;
+    for (long long round = 0; round < max_rounds; round++) {
+        // a chunk of trips
+        ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl + CTL_TRIPS, 0, sizeof(int), st));
+        if (exec) {
+            ENS_CUDA_CHECK(h, cudaGraphLaunch(exec, st));
+        } else {
+            for (int t = 0; t < chunk; t++) dispatch_body<double>(a, st);
+            ENS_LAUNCH_CHECK(h, "ens_solve_stream: loop kernels");
+        }
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(live.data(), a.w.live, lanes * sizeof(int), cudaMemcpyDeviceToHost, st));
+        ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+        // finished lanes give their outcome back and take the next samples
+        list.clear();
+        for (int L = 0; L < lanes; L++)
+            if (lane_sample[L] >= 0 && !live[L]) list.push_back(L);
+        const int nh = (int)list.size();
+        if (nh) {
+            ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.list, list.data(), nh * 4, cudaMemcpyHostToDevice, st));
+            k_harvest<<<nh, 256, 0, st>>>(nh, sw.list, J, S, sw.lane_sample, sw.x, w, sw.lane_iters, sw.lane_status,
+                                          sw.lane_relres, iters, status, relres, qoi);
+            ENS_LAUNCH_CHECK(h, "ens_solve_stream: harvest");
+        }
+        int nref = 0;
+        std::fill(refill.begin(), refill.end(), 0);
+        for (int i = 0; i < nh; i++) {
+            const int L = list[i];
+            if (next < M) {
+                lane_sample[L] = queue[next++];
+                refill[L] = 1;
+                nref++;
+            } else {
+                lane_sample[L] = -1;
+            }
+        }
+        int nlive = 0;
+        for (int L = 0; L < lanes; L++) nlive += (lane_sample[L] >= 0);
+        if (nlive == 0) break;
+        // the harvest kernel reads lane_sample: update it only after the harvest is queued
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.lane_sample, lane_sample.data(), lanes * 4, cudaMemcpyHostToDevice, st));
+        if (nref) {
+            ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.refill, refill.data(), lanes, cudaMemcpyHostToDevice, st));
+            ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.active, refill.data(), lanes, cudaMemcpyHostToDevice, st));
+            k_gather_xi<<<(lanes + 255) / 256, 256, 0, st>>>(lanes, N, sw.refill, sw.lane_sample, xi, sw.lane_xi);
+            rc = assemble_lanes(h, p, S, E, sw.lane_xi, sw.rowptr, sw.vals, 0, sw.dinv, sw.b, sw.refill, st);
+            if (rc) return rc;
+            Args ra = a;
+            ra.refill = sw.refill;
+            dispatch_init<double>(ra, st);
+            ENS_LAUNCH_CHECK(h, "ens_solve_stream: refill");
+        }
+        // queue drained: gather the live lanes into the first ensembles
+        if (next >= M && !repacked_all) {
+            const int target = (nlive + S - 1) / S;
+            std::vector<int> src, dst;
+            for (int L = target * S; L < lanes; L++)
+                if (lane_sample[L] >= 0) src.push_back(L);
+            for (int L = 0; L < target * S && dst.size() < src.size(); L++)
+                if (lane_sample[L] < 0) dst.push_back(L);
+            if (!src.empty() && dst.size() == src.size()) {
+                list.clear();
+                for (size_t i = 0; i < src.size(); i++) {
+                    list.push_back(src[i]);
+                    list.push_back(dst[i]);
+                    lane_sample[dst[i]] = lane_sample[src[i]];
+                    lane_sample[src[i]] = -1;
+                }
+                const int nm = (int)src.size();
+                ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.list, list.data(), nm * 8, cudaMemcpyHostToDevice, st));
+                dim3 grid(64, nm);
+                k_repack<<<grid, 256, 0, st>>>(nm, sw.list, J, nnz, S, N, sw);
+                k_count_live<<<(E + 127) / 128, 128, 0, st>>>(E, S, a.w.live, a.w.ens_live);
+                ENS_LAUNCH_CHECK(h, "ens_solve_stream: re-pack");
+            }
+            if (target <= 1) repacked_all = true;
+        }
     }
     return ENS_OK;
 }
@@ -1113,6 +1445,7 @@ extern "C" int ens_pcg_solve_static(ens_handle h, int J, int64_t nnz, int S, int
     a.J = J; a.S = S; a.E = E; a.maxit = maxit; a.nnz = nnz; a.rtol = rtol; a.g = g;
     a.rowptr = rowptr; a.colidx = colidx; a.vals = vals; a.dinv = dinv; a.b = b; a.x = x;
     a.active = active; a.iters = iters; a.status = status; a.relres = relres;
+    a.trip_cap = maxit;
     layout(J, S, E, g, &a.w, (char *)scratch);
     // The array keeps the previous call's contents: run_solve clears the
     // counters and the loop control; everything else is written before it is read.

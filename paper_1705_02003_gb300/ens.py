@@ -25,7 +25,8 @@ EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "e
            "ens_assemble", "ens_pcg_workspace_size", "ens_pcg_solve", "ens_group", "ens_sort_chunk",
            "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv",
            "ens_pcg_solve_static", "ens_pcg_ir_workspace_size", "ens_pcg_solve_ir",
-           "ens_adjoint_workspace_size", "ens_adjoint_grad", "ens_param_indicator")
+           "ens_adjoint_workspace_size", "ens_adjoint_grad", "ens_param_indicator",
+           "ens_stream_workspace_size", "ens_solve_stream")
 
 _lib = None
 _lock = threading.Lock()
@@ -78,6 +79,10 @@ def _declare(L):
     L.ens_sg_eval.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_int, vp, vp, vp, vp]
     L.ens_qoi.argtypes = [vp, c.c_int, c.c_int, c.c_int, vp, vp, vp, vp]
     L.ens_spmv.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_stream_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
+    L.ens_stream_workspace_size.restype = c.c_size_t
+    L.ens_solve_stream.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, vp, vp, vp, c.c_double,
+                                   c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
     L.ens_param_indicator.argtypes = [vp, c.POINTER(Problem), c.c_int, vp, vp, vp]
     L.ens_adjoint_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
     L.ens_adjoint_workspace_size.restype = c.c_size_t
@@ -253,6 +258,34 @@ def ens_pcg_solve_ir(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx
                                  _ptr(outer_its), _ptr(relres), _ptr(status), _ptr(work), work.numel(),
                                  _stream(stream))
     h.check(rc, "ens_pcg_solve_ir")
+
+
+def ens_stream_workspace_size(prob: Problem, S: int, E: int) -> int:
+    return int(load().ens_stream_workspace_size(ctypes.byref(prob), int(S), int(E)))
+
+
+def ens_solve_stream(h: Handle, prob: Problem, S: int, E: int, xi, order, rtol: float, maxit: int, chunk: int,
+                     iters, status, relres, qoi=None, w=None, work=None, stream=None):
+    """Continuous ensemble batching of the samples xi[M][N] (see include/ens.h)."""
+    M = iters.numel()
+    _check_dtype(xi, torch.float64, "xi")
+    for t, nm, dt in ((iters, "iters", torch.int32), (status, "status", torch.int32),
+                      (relres, "relres", torch.float64)):
+        _check_dtype(t, dt, nm)
+    if order is not None:
+        _check_dtype(order, torch.int32, "order")
+    if qoi is not None:
+        _check_dtype(qoi, torch.float64, "qoi")
+    if w is not None:
+        _check_dtype(w, torch.float64, "w")
+    if xi.numel() != M * prob.nparam:
+        raise ValueError("xi must be [M][nparam]")
+    if work is None:
+        work = torch.empty(ens_stream_workspace_size(prob, S, E), dtype=torch.uint8, device=xi.device)
+    rc = load().ens_solve_stream(h.ptr, ctypes.byref(prob), int(S), int(E), int(M), _ptr(xi), _ptr(order), _ptr(w),
+                                 float(rtol), int(maxit), int(chunk), _ptr(iters), _ptr(status), _ptr(relres),
+                                 _ptr(qoi), _ptr(work), work.numel(), _stream(stream))
+    h.check(rc, "ens_solve_stream")
 
 
 def ens_param_indicator(h: Handle, prob: Problem, xi, H, stream=None):

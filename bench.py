@@ -448,11 +448,11 @@ def run_layers(h, stream):
     prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
     M, lanes = 256, 64
     xi = torch.from_numpy(inputs.draws(wl.samples, wl.nparam, seed=wl.seed)[:M]).cuda()
-    best_S, tune = batching.autotune(h, prob, xi, lanes=lanes, rtol=wl.rtol, maxit=wl.maxit, chunk=64,
+    best_S, tune = batching.autotune(h, prob, xi, lanes=lanes, rtol=wl.rtol, maxit=wl.maxit, chunk=32,
                                      stream=stream)
     E = lanes // best_S
     work = torch.empty(ens.ens_stream_workspace_size(prob, best_S, E), dtype=torch.uint8, device="cuda")
-    res, tstream = timed(lambda: batching.solve_stream(h, prob, xi, best_S, E, wl.rtol, wl.maxit, chunk=64,
+    res, tstream = timed(lambda: batching.solve_stream(h, prob, xi, best_S, E, wl.rtol, wl.maxit, chunk=32,
                                                        work=work))
     del work
     fsol = EnsembleSolver(h, prob, best_S, lanes, wl.rtol, wl.maxit)

@@ -94,19 +94,26 @@ __device__ __forceinline__ void put(V *vals, long long idx, double v) { vals[idx
 template <typename V>
 __global__ void k_assemble_fd5(int n, int N, double aniso, int S, int E, const double *__restrict__ xi,
                                const int32_t *__restrict__ rowptr, V *__restrict__ vals,
-                               double *__restrict__ dinv, double *__restrict__ b, long long nnz, const uint8_t *__restrict__ lane_mask)
+                               double *__restrict__ dinv, double *__restrict__ b, long long nnz, const int32_t *__restrict__ lanes, int nlanes)
 {
     const int J = n * n;
-    const long long total = (long long)E * J * S;
+    const long long total = lanes ? (long long)nlanes * J : (long long)E * J * S;
     const double den = (double)(n + 1);
     const double ih2 = den * den;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        int s = (int)(t % S);
-        long long er = t / S;
-        int row = (int)(er % J);
-        int e = (int)(er / J);
-        if (lane_mask && !lane_mask[e * S + s]) continue;
+        int s, row, e;
+        if (lanes) {  // one refilled lane after another: rows of a lane are consecutive threads
+            const int L = lanes[t / J];
+            row = (int)(t % J);
+            e = L / S;
+            s = L % S;
+        } else {
+            s = (int)(t % S);
+            long long er = t / S;
+            row = (int)(er % J);
+            e = (int)(er / J);
+        }
         double x[8];
         const double *xs = xi + ((long long)e * S + s) * N;
         for (int k = 0; k < N; k++) x[k] = xs[k];
@@ -136,20 +143,27 @@ __global__ void k_assemble_fd5(int n, int N, double aniso, int S, int E, const d
 template <typename V>
 __global__ void k_assemble_fd7(int n, double aniso, int S, int E, const double *__restrict__ xi,
                                const int32_t *__restrict__ rowptr, V *__restrict__ vals,
-                               double *__restrict__ dinv, double *__restrict__ b, long long nnz, const uint8_t *__restrict__ lane_mask)
+                               double *__restrict__ dinv, double *__restrict__ b, long long nnz, const int32_t *__restrict__ lanes, int nlanes)
 {
     const int n2 = n * n;
     const int J = n2 * n;
-    const long long total = (long long)E * J * S;
+    const long long total = lanes ? (long long)nlanes * J : (long long)E * J * S;
     const double den = (double)(n + 1);
     const double ih2 = den * den;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        int s = (int)(t % S);
-        long long er = t / S;
-        int row = (int)(er % J);
-        int e = (int)(er / J);
-        if (lane_mask && !lane_mask[e * S + s]) continue;
+        int s, row, e;
+        if (lanes) {  // one refilled lane after another: rows of a lane are consecutive threads
+            const int L = lanes[t / J];
+            row = (int)(t % J);
+            e = L / S;
+            s = L % S;
+        } else {
+            s = (int)(t % S);
+            long long er = t / S;
+            row = (int)(er % J);
+            e = (int)(er / J);
+        }
         double x[6];
         const double *xs = xi + ((long long)e * S + s) * 6;
         for (int k = 0; k < 6; k++) x[k] = xs[k];
@@ -189,18 +203,25 @@ __device__ __forceinline__ double q1_sign(int u) { return u ? 1.0 : -1.0; }
 template <typename V>
 __global__ void k_assemble_q1(int n, double aniso, int S, int E, const double *__restrict__ xi,
                               const int32_t *__restrict__ rowptr, V *__restrict__ vals,
-                              double *__restrict__ dinv, double *__restrict__ b, long long nnz, const uint8_t *__restrict__ lane_mask)
+                              double *__restrict__ dinv, double *__restrict__ b, long long nnz, const int32_t *__restrict__ lanes, int nlanes)
 {
     const int J = n * n;
-    const long long total = (long long)E * J * S;
+    const long long total = lanes ? (long long)nlanes * J : (long long)E * J * S;
     const double den = (double)(n + 1);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        int s = (int)(t % S);
-        long long er = t / S;
-        int row = (int)(er % J);
-        int e = (int)(er / J);
-        if (lane_mask && !lane_mask[e * S + s]) continue;
+        int s, row, e;
+        if (lanes) {  // one refilled lane after another: rows of a lane are consecutive threads
+            const int L = lanes[t / J];
+            row = (int)(t % J);
+            e = L / S;
+            s = L % S;
+        } else {
+            s = (int)(t % S);
+            long long er = t / S;
+            row = (int)(er % J);
+            e = (int)(er / J);
+        }
         const double *xs = xi + ((long long)e * S + s) * 4;
         double x0 = xs[0], x1 = xs[1], x2 = xs[2], x3 = xs[3];
         int i = row % n, j = row / n;
@@ -396,33 +417,35 @@ extern "C" int ens_pattern(ens_handle h, const ens_problem *p, int32_t *rowptr, 
 
 namespace ens {
 int assemble_lanes(ens_ctx *h, const ens_problem *p, int S, int E, const double *xi, const int32_t *rowptr,
-                   void *vals, int vals_f32, double *dinv, double *b, const uint8_t *lane_mask, cudaStream_t st)
+                   void *vals, int vals_f32, double *dinv, double *b, const int32_t *lanes, int nlanes,
+                   cudaStream_t st)
 {
     int J;
     int64_t nnz;
     std::string why;
     int rc = problem_check(p, &J, &nnz, &why);
     if (rc) return set_error(h, rc, "ens_assemble: " + why);
-    long long total = (long long)E * J * S;
+    if (lanes && nlanes <= 0) return ENS_OK;
+    long long total = lanes ? (long long)nlanes * J : (long long)E * J * S;
     unsigned grid = grid_for(total, 256);
     switch (p->kind) {
     case ENS_FD5_LOGKL:
         if (vals_f32)
-            k_assemble_fd5<float><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lane_mask);
+            k_assemble_fd5<float><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lanes, nlanes);
         else
-            k_assemble_fd5<double><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lane_mask);
+            k_assemble_fd5<double><<<grid, 256, 0, st>>>(p->n, p->nparam, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lanes, nlanes);
         break;
     case ENS_Q1_ROT:
         if (vals_f32)
-            k_assemble_q1<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lane_mask);
+            k_assemble_q1<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lanes, nlanes);
         else
-            k_assemble_q1<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lane_mask);
+            k_assemble_q1<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lanes, nlanes);
         break;
     default:
         if (vals_f32)
-            k_assemble_fd7<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lane_mask);
+            k_assemble_fd7<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lanes, nlanes);
         else
-            k_assemble_fd7<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lane_mask);
+            k_assemble_fd7<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lanes, nlanes);
         break;
     }
     ENS_LAUNCH_CHECK(h, "ens_assemble: kernel launch");
@@ -458,7 +481,7 @@ extern "C" int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, co
     if (E < 0) return set_error(h, ENS_EINVAL, "ens_assemble: E < 0");
     if (E == 0) return ENS_OK;
     if (!xi || !rowptr || !colidx || !vals) return set_error(h, ENS_EINVAL, "ens_assemble: null pointer");
-    return assemble_lanes(h, p, S, E, xi, rowptr, vals, vals_f32, dinv, b, nullptr, (cudaStream_t)stream);
+    return assemble_lanes(h, p, S, E, xi, rowptr, vals, vals_f32, dinv, b, nullptr, 0, (cudaStream_t)stream);
 }
 
 extern "C" int ens_param_indicator(ens_handle h, const ens_problem *p, int M, const double *xi, double *H,

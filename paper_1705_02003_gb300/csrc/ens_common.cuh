@@ -105,9 +105,10 @@ __device__ __host__ inline int row_neighbours(int kind, int n, int row, int *col
 }
 
 int problem_check(const ens_problem *p, int *J, int64_t *nnz, std::string *why);
-// Assembly of the lanes whose lane_mask[e * S + s] is set (all lanes when NULL).
+// Assembly of the lanes listed in lanes[nlanes] (lane = e * S + s; all lanes when NULL).
 int assemble_lanes(ens_ctx *h, const ens_problem *p, int S, int E, const double *xi, const int32_t *rowptr,
-                   void *vals, int vals_f32, double *dinv, double *b, const uint8_t *lane_mask, cudaStream_t st);
+                   void *vals, int vals_f32, double *dinv, double *b, const int32_t *lanes, int nlanes,
+                   cudaStream_t st);
 // The problem's graph into caller memory (rowptr[J+1], colidx[nnz]).
 int pattern_into(ens_ctx *h, const ens_problem *p, int32_t *rowptr, int32_t *colidx, cudaStream_t st);
 

@@ -1293,7 +1293,7 @@ extern "C" int ens_solve_stream(ens_handle h, const ens_problem *p, int S, int E
         ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.active, act.data(), lanes, cudaMemcpyHostToDevice, st));
         k_gather_xi<<<(lanes + 255) / 256, 256, 0, st>>>(lanes, N, sw.refill, sw.lane_sample, xi, sw.lane_xi);
         ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.lane_sample, lane_sample.data(), lanes * 4, cudaMemcpyHostToDevice, st));
-        rc = assemble_lanes(h, p, S, E, sw.lane_xi, sw.rowptr, sw.vals, 0, sw.dinv, sw.b, nullptr, st);
+        rc = assemble_lanes(h, p, S, E, sw.lane_xi, sw.rowptr, sw.vals, 0, sw.dinv, sw.b, nullptr, 0, st);
         if (rc) return rc;
         ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)E * CNT_KINDS * sizeof(int), st));
         ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl, 0, 2 * sizeof(int), st));
@@ -1347,10 +1347,15 @@ extern "C" int ens_solve_stream(ens_handle h, const ens_problem *p, int S, int E
         // the harvest kernel reads lane_sample: update it only after the harvest is queued
         ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.lane_sample, lane_sample.data(), lanes * 4, cudaMemcpyHostToDevice, st));
         if (nref) {
+            std::vector<int32_t> rl;
+            for (int L = 0; L < lanes; L++)
+                if (refill[L]) rl.push_back(L);
             ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.refill, refill.data(), lanes, cudaMemcpyHostToDevice, st));
             ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.active, refill.data(), lanes, cudaMemcpyHostToDevice, st));
+            ENS_CUDA_CHECK(h, cudaMemcpyAsync(sw.list, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, st));
             k_gather_xi<<<(lanes + 255) / 256, 256, 0, st>>>(lanes, N, sw.refill, sw.lane_sample, xi, sw.lane_xi);
-            rc = assemble_lanes(h, p, S, E, sw.lane_xi, sw.rowptr, sw.vals, 0, sw.dinv, sw.b, sw.refill, st);
+            rc = assemble_lanes(h, p, S, E, sw.lane_xi, sw.rowptr, sw.vals, 0, sw.dinv, sw.b, sw.list, (int)rl.size(),
+                                st);
             if (rc) return rc;
             Args ra = a;
             ra.refill = sw.refill;

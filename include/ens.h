@@ -112,6 +112,13 @@ int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, const double 
 int ens_param_indicator(ens_handle h, const ens_problem *p, int M, const double *xi, double *H,
                         void *stream);
 
+/* Number of independent loop branches ens_pcg_solve runs for E ensembles
+ * (no counterpart in the paper: a scheduling choice of this library): one per
+ * ensemble up to 16, or the value of the environment variable
+ * ENS_PCG_BRANCHES (n >= 1, capped at 16 and at E) read at ens_create; 1 in
+ * the host-loop mode.  Returns 0 for a NULL handle or E <= 0. */
+int ens_pcg_branches(ens_handle h, int E);
+
 /* Bytes of caller workspace ens_pcg_solve needs (device memory, 256-byte aligned). */
 size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E);
 
@@ -126,12 +133,14 @@ size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E);
  *   x[E][J][S]    output (written for every lane; 0 for inactive lanes).
  *   iters[E][S], relres[E][S], status[E][S]  outputs (relres = ||r||/||b||).
  *   work          caller scratch of at least ens_pcg_workspace_size bytes.
- * The iteration runs inside one CUDA graph with a device-evaluated while loop
- * (at most maxit trips), so the call does not synchronise the stream.  With
- * the environment variable ENS_PCG_HOST_LOOP=1 at ens_create, the same kernels
- * are instead launched from the host, which reads the live-lane count back
- * every 16 trips (a profiling aid: kernel profilers do not see kernels inside
- * a conditional graph body); results are identical. */
+ * The iteration runs inside one CUDA graph of ens_pcg_branches(h, E) device-
+ * evaluated while loops side by side, each over a contiguous range of the
+ * ensembles and at most maxit trips, so the call does not synchronise the
+ * stream and each range of ensembles stops on its own.  With the environment
+ * variable ENS_PCG_HOST_LOOP=1 at ens_create, the same kernels are instead
+ * launched from the host, which reads the live-lane count back every 16 trips
+ * (a profiling aid: kernel profilers do not see kernels inside a conditional
+ * graph body).  Results do not depend on either choice, bit for bit. */
 int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   const int32_t *rowptr, const int32_t *colidx, const double *vals,
                   const double *dinv, const double *b, double *x, const uint8_t *active,

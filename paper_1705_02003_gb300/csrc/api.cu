@@ -28,6 +28,9 @@ extern "C" int ens_create(ens_handle *out, int device)
     h->device = device;
     const char *hl = getenv("ENS_PCG_HOST_LOOP");
     h->host_loop = (hl && hl[0] == '1') ? 1 : 0;
+    const char *nb = getenv("ENS_PCG_BRANCHES");
+    h->branches = nb ? atoi(nb) : 0;
+    if (h->branches < 0) h->branches = 0;
     if (cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess) {
         delete h;
         return ENS_ECUDA;

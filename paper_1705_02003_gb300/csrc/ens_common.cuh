@@ -28,6 +28,7 @@ struct ens_ctx {
     std::vector<ens::GraphEntry> graphs;     // small LRU cache of instantiated loops
     uint64_t clock = 0;
     int host_loop = 0;                       // ENS_PCG_HOST_LOOP=1: launch the PCG loop from the host
+    int branches = 0;                        // ENS_PCG_BRANCHES=n: graph branches of a PCG loop (0: one per ensemble, at most 16)
 };
 
 namespace ens {

@@ -39,6 +39,10 @@ namespace ens {
 namespace {
 
 enum { CTL_NLIVE = 0, CTL_TRIPS = 1, CTL_OUTER_LIVE = 2, CTL_WORDS = 16 };
+// The PCG loop of a solve may run as several independent graph branches, each
+// over a contiguous range of ensembles with its own trip counter (the words
+// b * CTL_WORDS + CTL_TRIPS); CTL_NLIVE counts the live lanes of all of them.
+constexpr int kMaxBranches = 16;
 enum { CNT_INIT = 0, CNT_SPMV = 1, CNT_UPD = 2, CNT_RES = 3, CNT_KINDS = 4 };
 
 struct Ws {
@@ -48,7 +52,7 @@ struct Ws {
     int *k, *live;          // [E][S]
     int *ens_live;          // [E]
     int *counter;           // [E][CNT_KINDS]
-    int *ctl;               // [CTL_WORDS]
+    int *ctl;               // [kMaxBranches][CTL_WORDS]
 };
 
 struct Geo {
@@ -72,6 +76,7 @@ struct Args {
     double *pq_out;  // ens_spmv: write p^T q per lane here instead of alpha
     int in_graph;    // K4 drives the graph's while loop (else the host loops)
     int trip_cap;    // trips per launch of the loop (maxit, or the chunk of a streamed solve)
+    int branch;      // graph branch running these ensembles (its trip counter)
     const uint8_t *refill;  // K0: restart only these lanes, keep the others (NULL: all lanes)
     cudaGraphConditionalHandle cond;
 };
@@ -125,7 +130,7 @@ void lay_loop(Bump &m, int J, int S, int E, const Geo &g, size_t tsize, Ws *w)
     w->live = (int *)m.take(lane * 4);
     w->ens_live = (int *)m.take((size_t)E * 4);
     w->counter = (int *)m.take((size_t)E * CNT_KINDS * 4);
-    w->ctl = (int *)m.take(CTL_WORDS * 4);
+    w->ctl = (int *)m.take(kMaxBranches * CTL_WORDS * 4);
 }
 
 size_t layout(int J, int S, int E, const Geo &g, Ws *w, char *base)
@@ -523,12 +528,18 @@ __global__ void __launch_bounds__(kBlock) k_direction(Args a, const T *__restric
     using LG = VecGeo<T, S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
     const int e = blockIdx.y;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        // K3 has finished for every ensemble, so the live count is final here.
-        const int trips = a.w.ctl[CTL_TRIPS] + 1;
-        a.w.ctl[CTL_TRIPS] = trips;
-        const int more = (a.w.ctl[CTL_NLIVE] > 0) && (trips < a.trip_cap);
-        if (a.in_graph) cudaGraphSetConditional(a.cond, more ? 1u : 0u);
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+        // K3 has finished for every ensemble of this branch, so their live
+        // counts are final here: loop again while one of them has a live lane.
+        int any = 0;
+        for (int i = threadIdx.x; i < a.E; i += kBlock) any |= a.w.ens_live[i] > 0;
+        any = __syncthreads_or(any);
+        if (threadIdx.x == 0) {
+            int *trip = a.w.ctl + a.branch * CTL_WORDS + CTL_TRIPS;
+            const int trips = *trip + 1;
+            *trip = trips;
+            if (a.in_graph) cudaGraphSetConditional(a.cond, (any && trips < a.trip_cap) ? 1u : 0u);
+        }
     }
     if (a.w.ens_live[e] == 0) return;
     const int lane0 = (threadIdx.x % TPR) * V;
@@ -626,15 +637,67 @@ uint64_t bits(double d)
     return u;
 }
 
-// Instantiate (or reuse) the while-loop graph for these arguments.
+// The arguments of the ensembles [e0, e0 + Eb) alone: every per-ensemble and
+// per-lane array offset to e0, run as graph branch `branch`.
 template <typename T>
-int loop_graph(ens_ctx *h, Args a, cudaGraphExec_t *out)
+Args sub_args(const Args &a, int e0, int Eb, int branch)
+{
+    Args s = a;
+    const size_t ev = (size_t)e0 * a.J * a.S, en = (size_t)e0 * a.nnz * a.S, el = (size_t)e0 * a.S;
+    s.E = Eb;
+    s.branch = branch;
+    s.vals = (const T *)a.vals + en;
+    s.dinv = (const T *)a.dinv + ev;
+    s.b = a.b + ev;
+    s.x = (T *)a.x + ev;
+    if (a.active) s.active = a.active + el;
+    s.iters = a.iters + el;
+    s.status = a.status + el;
+    s.relres = a.relres + el;
+    if (a.pq_out) s.pq_out = a.pq_out + el;
+    if (a.refill) s.refill = a.refill + el;
+    s.w.r = (T *)a.w.r + ev;
+    s.w.p = (T *)a.w.p + ev;
+    s.w.q = (T *)a.w.q + ev;
+    s.w.part0 = a.w.part0 + (size_t)e0 * a.g.nblk * a.S;
+    s.w.part1 = a.w.part1 + (size_t)e0 * a.g.nblk * a.S;
+    s.w.bnorm = a.w.bnorm + el;
+    s.w.rz = a.w.rz + el;
+    s.w.alpha = a.w.alpha + el;
+    s.w.beta = a.w.beta + el;
+    s.w.rr = a.w.rr + el;
+    s.w.k = a.w.k + el;
+    s.w.live = a.w.live + el;
+    s.w.ens_live = a.w.ens_live + e0;
+    s.w.counter = a.w.counter + (size_t)e0 * CNT_KINDS;
+    return s;  // w.ctl stays shared: CTL_NLIVE counts every branch's lanes
+}
+
+// Graph branches for E ensembles: one per ensemble up to kMaxBranches.  Each
+// branch runs its own while loop, so ensembles advance independently: the
+// SpMV (FP64-bound) of one overlaps the vector updates (HBM-bound) of another,
+// no kernel waits for the slowest ensemble of the solve, and ensembles that
+// have finished launch nothing.  The kernels and the per-ensemble reduction
+// order are the same as with one branch, so the results are identical.
+int loop_branches(const ens_ctx *h, int E)
+{
+    int b = h->branches > 0 ? h->branches : kMaxBranches;
+    if (b > kMaxBranches) b = kMaxBranches;
+    return b < E ? b : (E > 0 ? E : 1);
+}
+
+// Instantiate (or reuse) the while-loop graph for these arguments: `branches`
+// conditional WHILE nodes side by side, branch b over the ensembles
+// [b E / branches, (b + 1) E / branches).
+template <typename T>
+int loop_graph(ens_ctx *h, Args a, int branches, cudaGraphExec_t *out)
 {
     std::vector<uint64_t> key = {bits(a.rowptr), bits(a.colidx), bits(a.vals), bits(a.dinv), bits(a.b),
                                  bits(a.x), bits(a.active), bits(a.iters), bits(a.status), bits(a.relres),
                                  bits(a.w.r), bits(a.w.part0), bits(a.w.live), (uint64_t)a.J, (uint64_t)a.S,
                                  (uint64_t)a.E, (uint64_t)a.maxit, (uint64_t)a.nnz, bits(a.rtol),
-                                 (uint64_t)a.g.nblk, (uint64_t)a.g.RT, (uint64_t)sizeof(T), (uint64_t)a.trip_cap};
+                                 (uint64_t)a.g.nblk, (uint64_t)a.g.RT, (uint64_t)sizeof(T), (uint64_t)a.trip_cap,
+                                 bits(a.refill), (uint64_t)branches};
     h->clock++;
     for (auto &ge : h->graphs)
         if (ge.key == key) {
@@ -644,40 +707,44 @@ int loop_graph(ens_ctx *h, Args a, cudaGraphExec_t *out)
         }
     cudaGraph_t g = nullptr;
     ENS_CUDA_CHECK(h, cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle cond;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return cuda_error(h, e, "cudaGraphConditionalHandleCreate");
-    }
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return cuda_error(h, e, "cudaGraphAddNode(conditional)");
-    }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    a.cond = cond;
-    a.in_graph = 1;
-    e = cudaStreamBeginCaptureToGraph(h->capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return cuda_error(h, e, "cudaStreamBeginCaptureToGraph");
-    }
-    dispatch_body<T>(a, h->capture);
-    cudaError_t le = cudaGetLastError();
-    cudaGraph_t captured = nullptr;
-    e = cudaStreamEndCapture(h->capture, &captured);
-    if (le != cudaSuccess || e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return cuda_error(h, le != cudaSuccess ? le : e, "capturing the PCG loop body");
+    for (int br = 0; br < branches; br++) {
+        const int e0 = (int)((long long)br * a.E / branches), e1 = (int)((long long)(br + 1) * a.E / branches);
+        Args ab = sub_args<T>(a, e0, e1 - e0, br);
+        cudaGraphConditionalHandle cond;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_error(h, e, "cudaGraphConditionalHandleCreate");
+        }
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_error(h, e, "cudaGraphAddNode(conditional)");
+        }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ab.cond = cond;
+        ab.in_graph = 1;
+        e = cudaStreamBeginCaptureToGraph(h->capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_error(h, e, "cudaStreamBeginCaptureToGraph");
+        }
+        dispatch_body<T>(ab, h->capture);
+        cudaError_t le = cudaGetLastError();
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(h->capture, &captured);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_error(h, le != cudaSuccess ? le : e, "capturing the PCG loop body");
+        }
     }
     cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
         return cuda_error(h, e, "cudaGraphInstantiate");
@@ -703,10 +770,13 @@ int loop_graph(ens_ctx *h, Args a, cudaGraphExec_t *out)
 
 // Run the whole PCG (init, loop, finish) for prepared arguments.
 template <typename T>
-int run_solve(ens_ctx *h, const Args &a, cudaStream_t st, bool host_loop)
+int run_solve(ens_ctx *h, const Args &a, cudaStream_t st, bool host_loop, int branches = 1)
 {
+    if (host_loop) branches = 1;
     ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.counter, 0, (size_t)a.E * CNT_KINDS * sizeof(int), st));
     ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl, 0, 2 * sizeof(int), st));
+    for (int br = 1; br < branches; br++)
+        ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl + br * CTL_WORDS + CTL_TRIPS, 0, sizeof(int), st));
     dispatch_init<T>(a, st);
     ENS_LAUNCH_CHECK(h, "PCG init kernel");
     if (host_loop) {
@@ -722,7 +792,7 @@ int run_solve(ens_ctx *h, const Args &a, cudaStream_t st, bool host_loop)
         }
     } else {
         cudaGraphExec_t exec;
-        int rc = loop_graph<T>(h, a, &exec);
+        int rc = loop_graph<T>(h, a, branches, &exec);
         if (rc) return rc;
         ENS_CUDA_CHECK(h, cudaGraphLaunch(exec, st));
     }
@@ -745,6 +815,12 @@ int check_solve_args(ens_ctx *h, const char *who, int J, int64_t nnz, int S, int
 }  // namespace ens
 
 using namespace ens;
+
+extern "C" int ens_pcg_branches(ens_handle h, int E)
+{
+    if (!h || E <= 0) return 0;
+    return h->host_loop ? 1 : loop_branches(h, E);
+}
 
 extern "C" size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E)
 {
@@ -777,7 +853,7 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
     a.active = active; a.iters = iters; a.status = status; a.relres = relres;
     a.trip_cap = maxit;
     layout(J, S, E, g, &a.w, (char *)work);
-    return run_solve<double>(h, a, (cudaStream_t)stream, h->host_loop != 0);
+    return run_solve<double>(h, a, (cudaStream_t)stream, h->host_loop != 0, loop_branches(h, E));
 }
 
 // ---- mixed precision: FP32 inner PCG inside FP64 iterative refinement ---------
@@ -1302,7 +1378,7 @@ extern "C" int ens_solve_stream(ens_handle h, const ens_problem *p, int S, int E
     }
     cudaGraphExec_t exec = nullptr;
     if (!h->host_loop) {
-        rc = loop_graph<double>(h, a, &exec);
+        rc = loop_graph<double>(h, a, 1, &exec);
         if (rc) return rc;
     }
     bool repacked_all = false;

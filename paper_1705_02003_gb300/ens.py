@@ -26,7 +26,7 @@ EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "e
            "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv",
            "ens_pcg_solve_static", "ens_pcg_ir_workspace_size", "ens_pcg_solve_ir",
            "ens_adjoint_workspace_size", "ens_adjoint_grad", "ens_param_indicator",
-           "ens_stream_workspace_size", "ens_solve_stream")
+           "ens_stream_workspace_size", "ens_solve_stream", "ens_pcg_branches")
 
 _lib = None
 _lock = threading.Lock()
@@ -69,6 +69,8 @@ def _declare(L):
     L.ens_pattern.argtypes = [vp, c.POINTER(Problem), vp, vp, vp]
     L.ens_assemble.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, c.c_int, vp,
                                vp, vp]
+    L.ens_pcg_branches.argtypes = [vp, c.c_int]
+    L.ens_pcg_branches.restype = c.c_int
     L.ens_pcg_workspace_size.argtypes = [c.c_int, c.c_int64, c.c_int, c.c_int]
     L.ens_pcg_workspace_size.restype = c.c_size_t
     L.ens_pcg_solve.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp,
@@ -198,6 +200,11 @@ def ens_assemble(h: Handle, prob: Problem, S: int, E: int, xi, rowptr, colidx, v
                              _ptr(colidx), _ptr(vals), int(vals.dtype == torch.float32), _ptr(dinv),
                              _ptr(b), _stream(stream))
     h.check(rc, "ens_assemble")
+
+
+def ens_pcg_branches(h: Handle, E: int) -> int:
+    """Independent while-loop branches ens_pcg_solve runs for E ensembles."""
+    return int(load().ens_pcg_branches(h.ptr, int(E)))
 
 
 def ens_pcg_workspace_size(J: int, nnz: int, S: int, E: int) -> int:

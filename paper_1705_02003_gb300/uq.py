@@ -80,16 +80,24 @@ class Adaptive:
                 self.sink(self.solver, M)
             G[order] = q
             I[order] = it.to(torch.float64)
-            self.solve_sets.append(np.arange(offset, offset + M))
+            self.solve_sets.append(offset + order.cpu().numpy())
         return G, I
 
     def kernel_launches(self, I: np.ndarray) -> int:
         """Kernels of libens launched by the last run: per solve call assembly,
-        PCG init, three kernels per device-loop trip, finish and QoI; plus the
-        grouping and surplus kernels counted in run()."""
+        PCG init, finish and QoI, and three kernels per trip of each loop
+        branch (a branch runs until the slowest sample of its ensembles stops);
+        plus the grouping and surplus kernels counted in run()."""
         n = self.launches
+        S = self.solver.S
         for pts in self.solve_sets:
-            n += 4 + 3 * max(1, int(I[pts].max()))
+            it = I[pts]
+            E = -(-len(it) // S)
+            nb = ens.ens_pcg_branches(self.h, E)
+            n += 4
+            for b in range(nb):
+                e0, e1 = b * E // nb, (b + 1) * E // nb
+                n += 3 * max(1, int(it[e0 * S:e1 * S].max()))
         return n
 
     def run(self, grouping: str = "sur", seed: int = 0, record_trips: bool = False):

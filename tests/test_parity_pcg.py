@@ -166,6 +166,45 @@ def test_batch_size_does_not_change_results(h):
     assert np.array_equal(batch["iters"][8:16], alone["iters"])
 
 
+def _handle_with(env: dict):
+    """A handle created while the environment holds `env` (read at ens_create)."""
+    import os
+
+    saved = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return ens.Handle(0)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def test_loop_branches_do_not_change_results(h):
+    """Five ensembles with different iteration counts: one graph branch per
+    ensemble (the default), two branches, one branch and the host loop give
+    the same solutions, counts and residuals bit for bit, and each branch
+    stops on its own (the maxit cap still applies per lane)."""
+    xi = inputs.draws(40, 4, seed=12)
+    xi[:8, 0] = 0.95  # a strongly anisotropic ensemble: many more iterations
+    ref = Case(h, "q1", 20, 4, 4.0, 8, xi).solve(1e-8, 5000)
+    assert ens.ens_pcg_branches(h, 5) == 5 and ens.ens_pcg_branches(h, 40) == 16
+    for env in ({"ENS_PCG_BRANCHES": "2"}, {"ENS_PCG_BRANCHES": "1"}, {"ENS_PCG_HOST_LOOP": "1"}):
+        h2 = _handle_with(env)
+        nb = ens.ens_pcg_branches(h2, 5)
+        assert nb == (1 if "ENS_PCG_HOST_LOOP" in env else int(env["ENS_PCG_BRANCHES"]))
+        got = Case(h2, "q1", 20, 4, 4.0, 8, xi).solve(1e-8, 5000)
+        for k in ("x", "iters", "status", "relres"):
+            assert np.array_equal(got[k], ref[k]), (env, k)
+        capped = Case(h2, "q1", 20, 4, 4.0, 8, xi).solve(1e-8, 7)
+        assert np.all(capped["iters"] == 7) and np.all(capped["status"] == ens.LANE_MAXIT)
+        h2.close()
+    it = ref["iters"].reshape(5, 8).max(axis=1)
+    assert it.max() > it.min()  # the branches really ran different trip counts
+
+
 # ---------------------------------------------------------------------------
 # degenerate cases and status codes
 # ---------------------------------------------------------------------------

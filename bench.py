@@ -300,7 +300,7 @@ def run_ours(args, wl):
     charged = sum(float(np.max(run["I"][a + perm[k:k + sol.S]]))
                   for (a, b), perm in zip(run["levels"], run["perms"]) for k in range(0, b - a, sol.S)) * sol.S
     b_alg = 8 * sol.nnz + 72 * sol.J + (4 * sol.nnz + 4 * (sol.J + 1)) / sol.S
-    fma_it = sol.nnz + 8 * sol.J  # K2: nnz + J, K3: 5 J, K4: 2 J per sample-iteration
+    fma_it = sol.nnz + 7 * sol.J  # K2: nnz + J, K3: 5 J (z = D^-1 r stored), K4: J per sample-iteration
     t_it = max(b_alg / (peak * 1e9), 2.0 * fma_it / (FP64_PEAK_TFLOPS * 1e12))
     path_roof = M / (charged * t_it)
     roofline["path"] = {"value": path_roof, "unit": "sample-solves/s", "frac": value / path_roof,

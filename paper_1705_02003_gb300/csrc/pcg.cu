@@ -46,7 +46,7 @@ constexpr int kMaxBranches = 16;
 enum { CNT_INIT = 0, CNT_SPMV = 1, CNT_UPD = 2, CNT_RES = 3, CNT_KINDS = 4 };
 
 struct Ws {
-    void *r, *p, *q;        // [E][J][S] of the loop's value type
+    void *r, *p, *q, *z;    // [E][J][S] of the loop's value type (z = D^-1 r)
     double *part0, *part1;  // [E][nblk][S]
     double *bnorm, *rz, *alpha, *beta, *rr;  // [E][S]
     int *k, *live;          // [E][S]
@@ -119,6 +119,7 @@ void lay_loop(Bump &m, int J, int S, int E, const Geo &g, size_t tsize, Ws *w)
     w->r = m.take(vec);
     w->p = m.take(vec);
     w->q = m.take(vec);
+    w->z = m.take(vec);
     w->part0 = (double *)m.take(part);
     w->part1 = (double *)m.take(part);
     w->bnorm = (double *)m.take(lane * 8);
@@ -443,11 +444,11 @@ __global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4)))
     }
 }
 
-// ---- K3: x += alpha p, r -= alpha q; r^T r and r^T D^-1 r -> convergence, beta ----
+// ---- K3: x += alpha p, r -= alpha q, z = D^-1 r; r^T r and r^T z -> convergence, beta ----
 template <typename T, int S>
 __global__ void __launch_bounds__(kBlock) k_update(Args a, T *__restrict__ xx, T *__restrict__ rr,
                                                    const T *__restrict__ pp, const T *__restrict__ qq,
-                                                   const T *__restrict__ dinv)
+                                                   const T *__restrict__ dinv, T *__restrict__ zz)
 {
     using LG = VecGeo<T, S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a, T *__restrict__ xx, T
         const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
         for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
             const size_t o = vb + (size_t)r * S;
-            Vec<T, V> xv, rv, pv, qv, dv;
+            Vec<T, V> xv, rv, pv, qv, dv, zv;
             xv.load(xx + o);
             rv.load(rr + o);
             pv.load_ro(pp + o);
@@ -478,15 +479,17 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a, T *__restrict__ xx, T
             dv.load_ro(dinv + o);
 #pragma unroll
             for (int v = 0; v < V; v++) {
+                zv.v[v] = T(0);
                 if (!lv[v]) continue;  // frozen lane: keep x and r
                 xv.v[v] = fma(al[v], pv.v[v], xv.v[v]);
                 rv.v[v] = fma(-al[v], qv.v[v], rv.v[v]);
-                const T z = dv.v[v] * rv.v[v];
+                zv.v[v] = dv.v[v] * rv.v[v];
                 acc[0][v] = fma(wide(rv.v[v]), wide(rv.v[v]), acc[0][v]);
-                acc[1][v] = fma(wide(rv.v[v]), wide(z), acc[1][v]);
+                acc[1][v] = fma(wide(rv.v[v]), wide(zv.v[v]), acc[1][v]);
             }
             xv.store(xx + o);
             rv.store(rr + o);
+            zv.store(zz + o);
         }
     }
     __shared__ double tot[2 * S];
@@ -520,10 +523,9 @@ __global__ void __launch_bounds__(kBlock) k_update(Args a, T *__restrict__ xx, T
     }
 }
 
-// ---- K4: p = D^-1 r + beta p; loop control -------------------------------------
+// ---- K4: p = z + beta p (z = D^-1 r from K3); loop control ----------------------
 template <typename T, int S>
-__global__ void __launch_bounds__(kBlock) k_direction(Args a, const T *__restrict__ rr,
-                                                      const T *__restrict__ dinv, T *__restrict__ pp)
+__global__ void __launch_bounds__(kBlock) k_direction(Args a, const T *__restrict__ zz, T *__restrict__ pp)
 {
     using LG = VecGeo<T, S>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
@@ -558,13 +560,12 @@ __global__ void __launch_bounds__(kBlock) k_direction(Args a, const T *__restric
     const int r0 = blockIdx.x * a.g.RT, r1 = min(a.J, r0 + a.g.RT);
     for (int r = r0 + threadIdx.x / TPR; r < r1; r += RPP) {
         const size_t o = vb + (size_t)r * S;
-        Vec<T, V> rv, dv, pv;
-        rv.load_ro(rr + o);
-        dv.load_ro(dinv + o);
+        Vec<T, V> zv, pv;
+        zv.load_ro(zz + o);
         pv.load(pp + o);
 #pragma unroll
         for (int v = 0; v < V; v++)
-            if (lv[v]) pv.v[v] = fma(be[v], pv.v[v], dv.v[v] * rv.v[v]);
+            if (lv[v]) pv.v[v] = fma(be[v], pv.v[v], zv.v[v]);
         pv.store(pp + o);
     }
 }
@@ -603,8 +604,8 @@ void launch_body(const Args &a, cudaStream_t st)
     dim3 grid(a.g.nblk, a.E);
     k_spmv<T, S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, (const T *)a.vals, (const T *)a.w.p, (T *)a.w.q);
     k_update<T, S><<<grid, kBlock, 0, st>>>(a, (T *)a.x, (T *)a.w.r, (const T *)a.w.p, (const T *)a.w.q,
-                                           (const T *)a.dinv);
-    k_direction<T, S><<<grid, kBlock, 0, st>>>(a, (const T *)a.w.r, (const T *)a.dinv, (T *)a.w.p);
+                                           (const T *)a.dinv, (T *)a.w.z);
+    k_direction<T, S><<<grid, kBlock, 0, st>>>(a, (const T *)a.w.z, (T *)a.w.p);
 }
 
 template <typename T, int S>
@@ -659,6 +660,7 @@ Args sub_args(const Args &a, int e0, int Eb, int branch)
     s.w.r = (T *)a.w.r + ev;
     s.w.p = (T *)a.w.p + ev;
     s.w.q = (T *)a.w.q + ev;
+    s.w.z = (T *)a.w.z + ev;
     s.w.part0 = a.w.part0 + (size_t)e0 * a.g.nblk * a.S;
     s.w.part1 = a.w.part1 + (size_t)e0 * a.g.nblk * a.S;
     s.w.bnorm = a.w.bnorm + el;
@@ -1132,7 +1134,7 @@ extern "C" int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E, 
         ENS_CUDA_CHECK(h, cudaMemcpyAsync(&olive, sa.w.ctl + CTL_OUTER_LIVE, sizeof(int), cudaMemcpyDeviceToHost, st));
         ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
         if (olive == 0) break;
-        rc = run_solve<float>(h, sa, st, h->host_loop != 0);
+        rc = run_solve<float>(h, sa, st, h->host_loop != 0, loop_branches(h, E));
         if (rc) return rc;
         switch (S) {
         case 1: launch_ir_update<1>(ia, x, st); break;
@@ -1377,15 +1379,17 @@ extern "C" int ens_solve_stream(ens_handle h, const ens_problem *p, int S, int E
         ENS_LAUNCH_CHECK(h, "ens_solve_stream: first fill");
     }
     cudaGraphExec_t exec = nullptr;
+    const int branches = h->host_loop ? 1 : loop_branches(h, E);
     if (!h->host_loop) {
-        rc = loop_graph<double>(h, a, 1, &exec);
+        rc = loop_graph<double>(h, a, branches, &exec);
         if (rc) return rc;
     }
     bool repacked_all = false;
     const long long max_rounds = ((long long)M / lanes + 2) * ((long long)maxit / chunk + 2) + 16;
     for (long long round = 0; round < max_rounds; round++) {
         // a chunk of trips
-        ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl + CTL_TRIPS, 0, sizeof(int), st));
+        for (int br = 0; br < branches; br++)
+            ENS_CUDA_CHECK(h, cudaMemsetAsync(a.w.ctl + br * CTL_WORDS + CTL_TRIPS, 0, sizeof(int), st));
         if (exec) {
             ENS_CUDA_CHECK(h, cudaGraphLaunch(exec, st));
         } else {

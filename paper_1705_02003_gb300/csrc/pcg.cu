@@ -244,12 +244,25 @@ __device__ bool reduce_lanes(double (&acc)[NS][LG::V], double *part_base[NS], in
     if (!s_last) return false;
     __threadfence();
     {
+        // Partials b = g, g + G, g + 2G, ... summed in that order; the loads
+        // are issued eight at a time so the tail is not one L2 round trip per term.
+        constexpr int U = 8;
         const int g = tid / S, s = tid % S;
 #pragma unroll
         for (int ns = 0; ns < NS; ns++) {
             double v = 0.0;
-            const double *pb = part_base[ns] + (size_t)e * nblk * S;
-            for (int b = g; b < nblk; b += LG::G) v = dadd(v, __ldcg(pb + (size_t)b * S + s));
+            const double *pb = part_base[ns] + (size_t)e * nblk * S + s;
+            for (int b0 = g; b0 < nblk; b0 += U * LG::G) {
+                double t[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int b = b0 + u * LG::G;
+                    t[u] = b < nblk ? __ldcg(pb + (size_t)b * S) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++)
+                    if (b0 + u * LG::G < nblk) v = dadd(v, t[u]);
+            }
             grp[g][ns][s] = v;
         }
     }

@@ -44,7 +44,7 @@ FP64_PEAK_SOURCE = "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 T
 
 # DRAM bytes of one K2 launch measured by ncu on the E = 8 case of the same
 # kernel (profiles/k_spmv_q1_256_E8.md), scaled by the units a launch processes.
-SPMV_TRAFFIC_PER_ENSEMBLE = {"q1_256_adaptive": (673.70368e6 + 39.161856e6) / 8}
+SPMV_TRAFFIC_PER_ENSEMBLE = {"q1_256_adaptive": (673.746432e6 + 39.087872e6) / 8}
 
 
 def spmv_traffic(wl, E):
@@ -261,6 +261,19 @@ def run_ours(args, wl):
         tp = e0.elapsed_time(e1) / 1e3
         extra["per_sample"] = {"value": M / tp, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r3["I"] - run["I"])))}
 
+    # per solve call (one per level): size, branches and time, from one more step
+    ad.time_calls = True
+    rl = ad.run("sur")
+    ad.time_calls = False
+    level_calls = []
+    for (M_c, ms), pts in zip(ad.call_times(), ad.solve_sets):
+        it = rl["I"][pts]
+        E_c = -(-M_c // ad.S)
+        charged_c = ad.S * sum(float(it[k:k + ad.S].max()) for k in range(0, M_c, ad.S))
+        level_calls.append({"M": M_c, "E": E_c, "branches": ens.ens_pcg_branches(h, E_c),
+                            "max_iters": int(it.max()), "ms": ms,
+                            "ps_per_row_lane_iteration": ms * 1e9 / (charged_c * ad.solver.J)})
+
     layers = {} if args.no_layers else run_layers(h, stream)
 
     # dominant kernel: the ensemble SpMV (K2) on a full-capacity batch
@@ -362,11 +375,11 @@ def run_ours(args, wl):
             "clocks": clk,
             "R": {"sur": R["run"][1], "its": R["its"][1]},
             "arms": extra,
+            "level_calls": level_calls,
             "layers": layers,
         }
         if "per_sample" in extra:
             line["speedup_vs_per_sample"] = value / extra["per_sample"]["value"]
-        # roofline of the whole solve: frozen lanes stream their values too
         print(json.dumps(line))
     h.close()
     return 0

@@ -57,6 +57,8 @@ class Adaptive:
         self.launches = 0
         self.solve_sets = []
         self.sink = None  # optional callable(solver, M) run after every solve call
+        self.time_calls = False  # record CUDA events around every ensemble solve call
+        self.call_events = []
 
     def _solve(self, y_dev: torch.Tensor, order: torch.Tensor, offset: int):
         """Solve the points y_dev[order] and return (G, I) in point order.
@@ -75,13 +77,25 @@ class Adaptive:
                 I[order[j:j + 1]] = it.to(torch.float64)
                 self.solve_sets.append(np.array([offset + order_h[j]]))
         else:
+            if self.time_calls:
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record()
             it, st, rr, q = self.solver.solve(xi)
+            if self.time_calls:
+                ev[1].record()
+                self.call_events.append((M, ev))
             if self.sink:
                 self.sink(self.solver, M)
             G[order] = q
             I[order] = it.to(torch.float64)
             self.solve_sets.append(offset + order.cpu().numpy())
         return G, I
+
+    def call_times(self):
+        """(M, milliseconds) of every ensemble solve call of the last run made
+        with time_calls set (synchronises the device)."""
+        torch.cuda.synchronize()
+        return [(M, ev[0].elapsed_time(ev[1])) for M, ev in self.call_events]
 
     def kernel_launches(self, I: np.ndarray) -> int:
         """Kernels of libens launched by the last run: per solve call assembly,
@@ -105,6 +119,7 @@ class Adaptive:
         N = wl.nparam
         self.launches = 0
         self.solve_sets = []
+        self.call_events = []
         lvl, idx = ens.ens_sg_initial(N, wl.init_level)
         y = coords(lvl, idx)
         lvl_d = torch.from_numpy(lvl).to(dev)

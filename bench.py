@@ -275,6 +275,8 @@ def run_ours(args, wl):
                             "ps_per_row_lane_iteration": ms * 1e9 / (charged_c * ad.solver.J)})
 
     layers = {} if args.no_layers else run_layers(h, stream)
+    configs = {} if args.no_layers else run_configs(h, stream)
+    pilot = {} if args.no_layers else run_pilot(h, stream)
 
     # dominant kernel: the ensemble SpMV (K2) on a full-capacity batch
     sol = ad.solver
@@ -377,12 +379,103 @@ def run_ours(args, wl):
             "arms": extra,
             "level_calls": level_calls,
             "layers": layers,
+            "spmv_configs": configs,
+            "pilot_grouping": pilot,
         }
         if "per_sample" in extra:
             line["speedup_vs_per_sample"] = value / extra["per_sample"]["value"]
         print(json.dumps(line))
     h.close()
     return 0
+
+
+def run_configs(h, stream):
+    """The ensemble SpMV (K2) on the other problem configurations, each with
+    inputs larger than L2: algorithmic GB/s and FP64 rate per launch."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens, inputs
+    from paper_1705_02003_gb300.solver import EnsembleSolver
+
+    peak, peak_kind = peaks()
+    out = {}
+    for name, E in (("fd7_64_batch", 4), ("fd7_128_mixed", 1), ("fd5_512_adjoint", 4)):
+        wl = inputs.WORKLOADS[name]
+        prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+        S = 32
+        sol = EnsembleSolver(h, prob, S, E * S, wl.rtol, wl.maxit)
+        xi = torch.from_numpy(inputs.draws(E * S, wl.nparam, seed=wl.seed)).cuda()
+        ens.ens_assemble(h, prob, S, E, xi.reshape(-1), sol.rowptr, sol.colidx, sol.vals, sol.dinv, sol.b)
+        q = torch.empty_like(sol.x)
+        pq = torch.empty(E * S, dtype=torch.float64, device="cuda")
+        call = lambda: ens.ens_spmv(h, sol.J, sol.nnz, S, E, sol.rowptr, sol.colidx, sol.vals, sol.b, q, pq,
+                                    sol.work)
+        for _ in range(3):
+            call()
+        reps = 10
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        byts = E * (8 * sol.nnz * S + 4 * sol.nnz + 4 * (sol.J + 1) + 16 * sol.J * S)
+        fma = E * S * (sol.nnz + sol.J)
+        out[name] = {"E": E, "S": S, "bytes_per_launch": byts, "launch_ms": t * 1e3,
+                     "hbm_gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / peak,
+                     "fp64_tflops": 2 * fma / t / 1e12, "fp64_frac": 2 * fma / t / 1e12 / FP64_PEAK_TFLOPS}
+        del sol, q
+    out["peaks"] = {"hbm_gbs": peak, "hbm_source": peak_kind, "fp64_tflops": FP64_PEAK_TFLOPS}
+    return out
+
+
+def run_pilot(h, stream):
+    """Surrogate grouping of a non-adaptive sample set (Section 5): the level-1
+    sparse grid of the 64^3 problem (256 points) is solved and its iteration
+    surrogate groups 512 of the 4096 uniform draws; surrogate order against
+    generation order, and R for S = 8..64 from the draws' iteration counts."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens, inputs, uq
+    from paper_1705_02003_gb300.solver import EnsembleSolver
+
+    wl = inputs.WORKLOADS["fd7_64_batch"]
+    prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    S, M = 32, 512
+    sol = EnsembleSolver(h, prob, S, M, wl.rtol, wl.maxit)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    pg = uq.PilotGrouping(h, sol, level=1)
+    _, t_pilot = timed(pg.build)
+    xi = torch.from_numpy(inputs.draws(wl.samples, wl.nparam, seed=wl.seed)[:M]).cuda()
+    (pred, perm, _), t_group = timed(lambda: pg.group(xi, S))
+    order = perm.to(torch.int64)
+    sol.solve(xi)  # warm-up (graph instantiation)
+    (it_nat, *_), t_nat = timed(lambda: sol.solve(xi))
+    it_nat = it_nat.cpu().numpy().astype(np.float64)
+    (it_sur, *_), t_sur = timed(lambda: sol.solve(xi.index_select(0, order)))
+    p = perm.cpu().numpy()
+    R = {}
+    for s_ in (8, 16, 32, 64):
+        R[s_] = {"sur": uq.work_ratio(s_, p, it_nat), "nat": uq.work_ratio(s_, np.arange(M), it_nat),
+                 "its": uq.work_ratio(s_, np.argsort(it_nat, kind="stable"), it_nat)}
+    return {"workload": wl.name, "pilot_points": len(pg.lvl), "draws": M, "S": S,
+            "pilot_seconds": t_pilot, "group_seconds": t_group,
+            "sur_value": M / t_sur, "nat_value": M / t_nat, "unit": "sample-solves/s",
+            "speedup_sur_vs_nat": t_nat / t_sur, "R": R,
+            "same_iterations": bool(np.array_equal(np.sort(it_sur.cpu().numpy()), np.sort(it_nat)))}
 
 
 def run_layers(h, stream):

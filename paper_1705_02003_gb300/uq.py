@@ -38,6 +38,64 @@ def work_ratio(S: int, perm: np.ndarray, iters: np.ndarray) -> float:
     return S * num / float(it.sum())
 
 
+def level_surpluses(h: ens.Handle, lvl: np.ndarray, lvl_d: torch.Tensor, idx_d: torch.Tensor,
+                    y_d: torch.Tensor, values: torch.Tensor) -> torch.Tensor:
+    """Surpluses c = v - (surrogate of the lower levels)(y) of a grid listed in
+    non-decreasing level order, one level at a time (Eq. hierSGint)."""
+    c = torch.empty(len(lvl), dtype=torch.float64, device=values.device)
+    lev = lvl.sum(axis=1)
+    for L in range(int(lev.max()) + 1):
+        a, b = int(np.searchsorted(lev, L, "left")), int(np.searchsorted(lev, L, "right"))
+        if b > a:
+            ens.ens_sg_eval(h, lvl_d[:a] if a else None, idx_d[:a], c[:a], y_d[a:b], c[a:b], values=values[a:b])
+    return c
+
+
+class PilotGrouping:
+    """Surrogate grouping of a sample set that is not generated adaptively
+    (Section 5: pre-select samples, evaluate them, and build the iteration
+    surrogate from the results).  The pre-selected samples are the full sparse
+    grid of levels 0..level; they are solved in ensembles of the solver's S in
+    generation order, their iteration counts are hierarchized level by level,
+    and a set of draws is then grouped by the surrogate's prediction (sort and
+    chunk, ens_group)."""
+
+    def __init__(self, handle: ens.Handle, solver: EnsembleSolver, level: int):
+        self.h = handle
+        self.solver = solver
+        self.level = level
+        self.lvl, self.idx = ens.ens_sg_initial(solver.N, level)
+        dev = solver.dev
+        self.lvl_d = torch.from_numpy(self.lvl).to(dev)
+        self.idx_d = torch.from_numpy(self.idx).to(dev)
+        self.y_d = torch.from_numpy(coords(self.lvl, self.idx)).to(dev)
+        self.I = None
+        self.cI = None
+
+    def build(self):
+        """Solve the pilot points and form the iteration surpluses."""
+        sol = self.solver
+        M = len(self.lvl)
+        cap = sol.Emax * sol.S
+        I = torch.empty(M, dtype=torch.float64, device=sol.dev)
+        for a in range(0, M, cap):
+            b = min(M, a + cap)
+            it, st, rr, q = sol.solve(self.y_d[a:b])
+            I[a:b] = it.to(torch.float64)
+        self.I = I
+        self.cI = level_surpluses(self.h, self.lvl, self.lvl_d, self.idx_d, self.y_d, I)
+        return self
+
+    def group(self, xi: torch.Tensor, S: int, pred: torch.Tensor | None = None):
+        """(pred, perm, n_ens) for the draws xi[M][N] (device f64, inside
+        [-1, 1]^N): predicted iterations, the ensemble order, the ensemble count."""
+        M = xi.shape[0]
+        pred = torch.empty(M, dtype=torch.float64, device=xi.device) if pred is None else pred
+        perm = torch.empty(M, dtype=torch.int32, device=xi.device)
+        n_ens = ens.ens_group(self.h, self.lvl_d, self.idx_d, self.cI, xi.contiguous(), S, pred, perm)
+        return pred, perm, n_ens
+
+
 class Adaptive:
     """Runs the loop for one workload with one grouping."""
 
@@ -129,17 +187,9 @@ class Adaptive:
         order = torch.arange(M0, device=dev)
         G, I = self._solve(y_d, order, 0)
         # surpluses of the initial grid, one level at a time (Eq. hierSGint)
-        cG = torch.empty(M0, dtype=torch.float64, device=dev)
-        cI = torch.empty(M0, dtype=torch.float64, device=dev)
-        lev = lvl.sum(axis=1)
-        for L in range(int(lev.max()) + 1):
-            a, b = int(np.searchsorted(lev, L, "left")), int(np.searchsorted(lev, L, "right"))
-            if b > a:
-                ens.ens_sg_eval(self.h, lvl_d[:a] if a else None, idx_d[:a], cG[:a], y_d[a:b], cG[a:b],
-                                values=G[a:b])
-                ens.ens_sg_eval(self.h, lvl_d[:a] if a else None, idx_d[:a], cI[:a], y_d[a:b], cI[a:b],
-                                values=I[a:b])
-                self.launches += 2
+        cG = level_surpluses(self.h, lvl, lvl_d, idx_d, y_d, G)
+        cI = level_surpluses(self.h, lvl, lvl_d, idx_d, y_d, I)
+        self.launches += 2 * len(np.unique(lvl.sum(axis=1)))
         levels = [(0, M0)]
         perms = [np.arange(M0, dtype=np.int32)]
         preds = [np.zeros(M0)]

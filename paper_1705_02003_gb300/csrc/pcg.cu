@@ -379,13 +379,25 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restric
 // ---- K2: q = A p and p^T q per lane -> alpha -----------------------------------
 constexpr int kChunk = 9;  // nonzeros loaded together per row (covers the 5/7/9-point rows)
 
-template <typename T, int S>
-__global__ void __launch_bounds__(kBlock, (S >= 64 ? 2 : (S == 1 ? 3 : 4)))
+// K2 variants: V_ lanes per thread, KC nonzeros of a row loaded at once (longer
+// rows continue chunk by chunk).  One lane per thread and KC = 9 suit the
+// 9-point rows, where the FP64 pipe is the limit and more warps keep it fed;
+// for short rows (5- and 7-point stencils, S of 16 or 32) two lanes per thread
+// put twice the bytes of a row in flight for the same column indices.  The
+// variant is a function of the pattern and S only, so the results still do not
+// depend on E, on lane position or on the other lanes.
+template <int S, int V_, int KC> struct SpmvOcc {
+    static constexpr int value = S == 1 ? 3 : (V_ == 1 ? 4 : (KC <= 5 ? 3 : 2));
+};
+
+template <typename T, int S, int V_, int KC>
+__global__ void __launch_bounds__(kBlock, (SpmvOcc<S, V_, KC>::value))
     k_spmv(Args a, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
            const T *__restrict__ vals_all, const T *__restrict__ p_all, T *__restrict__ q_all)
 {
-    using LG = SpmvGeo<S>;
+    using LG = LaneGeo<S, V_>;
     constexpr int V = LG::V, TPR = LG::TPR, RPP = LG::RPP;
+    constexpr int kChunk = KC;
     const int e = blockIdx.y;
     if (a.w.ens_live[e] == 0) return;
     const int lane0 = (threadIdx.x % TPR) * V;
@@ -604,18 +616,38 @@ __global__ void k_spmv_prep(Args a)
     if (L < a.E) a.w.ens_live[L] = a.S;
 }
 
+// The K2 variant for S and the pattern's mean row length (see k_spmv).
+template <typename T, int S>
+void launch_k2(const Args &a, cudaStream_t st)
+{
+    dim3 grid(a.g.nblk, a.E);
+    const double row = (double)a.nnz / a.J;
+    const T *vals = (const T *)a.vals, *p = (const T *)a.w.p;
+    T *q = (T *)a.w.q;
+    if constexpr (S == 16 || S == 32) {
+        if (row <= 5.5) {
+            k_spmv<T, S, 2, 5><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
+            return;
+        }
+        if (row <= 7.5) {
+            k_spmv<T, S, 2, 7><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
+            return;
+        }
+    }
+    k_spmv<T, S, SpmvGeo<S>::V, 9><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
+}
+
 template <typename T, int S>
 void launch_spmv(const Args &a, cudaStream_t st)
 {
-    dim3 grid(a.g.nblk, a.E);
-    k_spmv<T, S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, (const T *)a.vals, (const T *)a.w.p, (T *)a.w.q);
+    launch_k2<T, S>(a, st);
 }
 
 template <typename T, int S>
 void launch_body(const Args &a, cudaStream_t st)
 {
     dim3 grid(a.g.nblk, a.E);
-    k_spmv<T, S><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, (const T *)a.vals, (const T *)a.w.p, (T *)a.w.q);
+    launch_k2<T, S>(a, st);
     k_update<T, S><<<grid, kBlock, 0, st>>>(a, (T *)a.x, (T *)a.w.r, (const T *)a.w.p, (const T *)a.w.q,
                                            (const T *)a.dinv, (T *)a.w.z);
     k_direction<T, S><<<grid, kBlock, 0, st>>>(a, (const T *)a.w.z, (T *)a.w.p);

@@ -382,12 +382,14 @@ constexpr int kChunk = 9;  // nonzeros loaded together per row (covers the 5/7/9
 // K2 variants: V_ lanes per thread, KC nonzeros of a row loaded at once (longer
 // rows continue chunk by chunk).  One lane per thread and KC = 9 suit the
 // 9-point rows, where the FP64 pipe is the limit and more warps keep it fed;
-// for short rows (5- and 7-point stencils, S of 16 or 32) two lanes per thread
-// put twice the bytes of a row in flight for the same column indices.  The
+// for short FP64 rows (the 5-point stencil, S of 16 or 32) two lanes per
+// thread put twice the bytes of a row in flight for the same column indices
+// (measured: 5-point 0.70 -> 0.45 ms per launch; for 7-point rows the variant
+// gained at large batches but lost with one or two ensembles, and in FP32).  The
 // variant is a function of the pattern and S only, so the results still do not
 // depend on E, on lane position or on the other lanes.
 template <int S, int V_, int KC> struct SpmvOcc {
-    static constexpr int value = S == 1 ? 3 : (V_ == 1 ? 4 : (KC <= 5 ? 3 : 2));
+    static constexpr int value = S == 1 ? 3 : (V_ == 1 ? 4 : 3);
 };
 
 template <typename T, int S, int V_, int KC>
@@ -624,13 +626,9 @@ void launch_k2(const Args &a, cudaStream_t st)
     const double row = (double)a.nnz / a.J;
     const T *vals = (const T *)a.vals, *p = (const T *)a.w.p;
     T *q = (T *)a.w.q;
-    if constexpr (S == 16 || S == 32) {
+    if constexpr (sizeof(T) == 8 && (S == 16 || S == 32)) {
         if (row <= 5.5) {
             k_spmv<T, S, 2, 5><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
-            return;
-        }
-        if (row <= 7.5) {
-            k_spmv<T, S, 2, 7><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
             return;
         }
     }

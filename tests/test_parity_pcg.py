@@ -101,6 +101,8 @@ SOLVE_CASES = [
     ("fd5", 16, 2, 3.0, 1, 5),
     ("fd5", 16, 2, 3.0, 2, 5),
     ("fd5", 16, 3, 3.0, 64, 70),
+    ("fd5", 40, 8, 3.0, 32, 45),    # 5-point rows at S = 16, 32: the two-lane SpMV variant
+    ("fd5", 50, 4, 3.0, 16, 20),    # (J = 1600, 2500: ragged last tile)
 ]
 
 
@@ -136,9 +138,10 @@ def test_pcg_full_size_sampled_lanes(h, name, lanes):
 # ---------------------------------------------------------------------------
 # invariants (bit-exact on the GPU)
 # ---------------------------------------------------------------------------
-def test_masked_lane_equals_full_ensemble_and_order_free(h):
+@pytest.mark.parametrize("kind,n", [("q1", 24), ("fd5", 40)])  # one and two lanes per SpMV thread
+def test_masked_lane_equals_full_ensemble_and_order_free(h, kind, n):
     xi = inputs.draws(16, 4, seed=5)
-    c = Case(h, "q1", 24, 4, 4.0, 16, xi)
+    c = Case(h, kind, n, 4, 4.0 if kind == "q1" else 3.0, 16, xi)
     full = c.solve(1e-8, 5000)
     again = c.solve(1e-8, 5000)
     for k in ("x", "iters", "status", "relres"):
@@ -152,7 +155,7 @@ def test_masked_lane_equals_full_ensemble_and_order_free(h):
         others = [L for L in range(16) if L != s]
         assert np.all(one["status"][others] == ens.LANE_INACTIVE)
     perm = np.random.default_rng(1).permutation(16)
-    cp = Case(h, "q1", 24, 4, 4.0, 16, xi[perm])
+    cp = Case(h, kind, n, 4, 4.0 if kind == "q1" else 3.0, 16, xi[perm])
     pp = cp.solve(1e-8, 5000)
     assert np.array_equal(pp["x"], full["x"][perm])
     assert np.array_equal(pp["iters"], full["iters"][perm])
@@ -275,7 +278,8 @@ def test_argument_errors(h):
 
 
 @pytest.mark.parametrize("kind,n,N,aniso,S,M", [("q1", 30, 4, 4.0, 16, 20), ("fd7", 9, 6, 3.0, 8, 9),
-                                                ("fd5", 20, 8, 3.0, 1, 3), ("fd5", 12, 2, 3.0, 64, 64)])
+                                                ("fd5", 20, 8, 3.0, 1, 3), ("fd5", 12, 2, 3.0, 64, 64),
+                                                ("fd5", 50, 4, 3.0, 16, 20), ("fd5", 40, 8, 3.0, 32, 33)])
 def test_spmv_matches_oracle_and_lane_dots(h, kind, n, N, aniso, S, M):
     """K2 alone: each row sum is taken in the oracle's column order, with one
     rounding per fused multiply-add instead of two, so every row agrees with

@@ -133,6 +133,14 @@ def barrier(pg):
         pg.barrier()
 
 
+def replica_rate(pg, world: int, samples: int, t_local: float):
+    """Whole-job rate of `world` independent replicas, each of which solved
+    `samples` samples in t_local seconds: the slowest rank bounds the job.
+    Returns (samples per second over all ranks, the slowest rank's seconds)."""
+    tmax = allmax(pg, t_local)
+    return world * samples / tmax, tmax
+
+
 def allmax(pg, v):
     if pg is None:
         return v
@@ -233,8 +241,7 @@ def run_ours(args, wl):
     barrier(pg)
     clk = clocks.stop()
     t = ev0.elapsed_time(ev1) / 1e3
-    tmax = allmax(pg, t)
-    value = world * M * args.steps / tmax
+    value, tmax = replica_rate(pg, world, M * args.steps, t)
     R = ratios(run)
 
     extra = {}

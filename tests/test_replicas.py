@@ -1,0 +1,64 @@
+"""The multi-process path of bench.py on CPU (gloo, world size 2).  The ensemble
+solve does not shard with an exchange: N GPUs run N independent replicas, and
+the only cross-rank steps are a barrier and the max over ranks of the timed
+region.  Rank 0 alone prints; the reference arm runs on rank 0 only."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        bench.barrier(dist)
+        value, tmax = bench.replica_rate(dist, world, 265, 1.0 + rank)  # rank 1 is the slow one
+        out.put((rank, value, tmax))
+        bench.barrier(dist)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_rate_takes_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.SimpleQueue()
+    mp.start_processes(_rank_main, args=(2, _free_port(), q), nprocs=2, join=True, start_method="spawn")
+    got = sorted(q.get() for _ in range(2))
+    for rank, value, tmax in got:
+        assert tmax == 2.0
+        assert value == pytest.approx(2 * 265 / 2.0)
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """bench.py --impl reference with two ranks: rank 0 times the oracle on a
+    tiny sample and prints one JSON line, rank 1 exits 0 without work."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-samples", "2",
+           "--workload", "fd5_32_adaptive"]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0

@@ -112,6 +112,17 @@ int ens_assemble(ens_handle h, const ens_problem *p, int S, int E, const double 
 int ens_param_indicator(ens_handle h, const ens_problem *p, int M, const double *xi, double *H,
                         void *stream);
 
+/* Validate a CSR graph (no counterpart in the paper: a guard of this
+ * library).  Checks rowptr[0] == 0, rowptr[J] == nnz, rowptr non-decreasing
+ * with every entry in [0, nnz], and every colidx entry in [0, J); reads only
+ * rowptr[0..J] and colidx[0..nnz).  Returns ENS_OK, or ENS_EINVAL with the
+ * failed checks in ens_last_error.  Synchronises `stream`.  With the
+ * environment variable ENS_CHECK=1 at ens_create, ens_pcg_solve,
+ * ens_pcg_solve_ir, ens_pcg_solve_static and ens_spmv run this check on their
+ * graph first and return its error without launching anything else. */
+int ens_check_pattern(ens_handle h, int J, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                      void *stream);
+
 /* Number of independent loop branches ens_pcg_solve runs for E ensembles
  * (no counterpart in the paper: a scheduling choice of this library): one per
  * ensemble up to 16, or the value of the environment variable

@@ -31,7 +31,14 @@ extern "C" int ens_create(ens_handle *out, int device)
     const char *nb = getenv("ENS_PCG_BRANCHES");
     h->branches = nb ? atoi(nb) : 0;
     if (h->branches < 0) h->branches = 0;
+    const char *ck = getenv("ENS_CHECK");
+    h->check = (ck && ck[0] == '1') ? 1 : 0;
     if (cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return ENS_ECUDA;
+    }
+    if (cudaMalloc(&h->check_flag, sizeof(int)) != cudaSuccess) {
+        cudaStreamDestroy(h->capture);
         delete h;
         return ENS_ECUDA;
     }
@@ -47,6 +54,7 @@ extern "C" int ens_destroy(ens_handle h)
         if (g.graph) cudaGraphDestroy(g.graph);
     }
     if (h->capture) cudaStreamDestroy(h->capture);
+    if (h->check_flag) cudaFree(h->check_flag);
     delete h;
     return ENS_OK;
 }

@@ -29,6 +29,8 @@ struct ens_ctx {
     uint64_t clock = 0;
     int host_loop = 0;                       // ENS_PCG_HOST_LOOP=1: launch the PCG loop from the host
     int branches = 0;                        // ENS_PCG_BRANCHES=n: graph branches of a PCG loop (0: one per ensemble, at most 16)
+    int check = 0;                           // ENS_CHECK=1: validate the caller's CSR graph before a solve
+    int *check_flag = nullptr;               // device word for the graph check
 };
 
 namespace ens {
@@ -105,6 +107,8 @@ __device__ __host__ inline int row_neighbours(int kind, int n, int row, int *col
     return c;
 }
 
+int check_pattern(ens_ctx *h, const char *who, int J, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                  cudaStream_t st);
 int problem_check(const ens_problem *p, int *J, int64_t *nnz, std::string *why);
 // Assembly of the lanes listed in lanes[nlanes] (lane = e * S + s; all lanes when NULL).
 int assemble_lanes(ens_ctx *h, const ens_problem *p, int S, int E, const double *xi, const int32_t *rowptr,

@@ -887,6 +887,10 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
         return set_error(h, ENS_EINVAL, "ens_pcg_solve: null pointer");
     if (((uintptr_t)vals | (uintptr_t)dinv | (uintptr_t)b | (uintptr_t)x | (uintptr_t)work) & 15)
         return set_error(h, ENS_EINVAL, "ens_pcg_solve: arrays must be 16-byte aligned");
+    if (h->check) {
+        int crc = check_pattern(h, "ens_pcg_solve", J, nnz, rowptr, colidx, (cudaStream_t)stream);
+        if (crc) return crc;
+    }
     Geo g = geometry(J, S);
     const size_t need = layout(J, S, E, g, nullptr, nullptr);
     if (work_bytes < need)
@@ -1141,6 +1145,10 @@ extern "C" int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E, 
         return set_error(h, ENS_EINVAL, "ens_pcg_solve_ir: null pointer");
     if (((uintptr_t)vals | (uintptr_t)vals32 | (uintptr_t)dinv | (uintptr_t)b | (uintptr_t)x | (uintptr_t)work) & 15)
         return set_error(h, ENS_EINVAL, "ens_pcg_solve_ir: arrays must be 16-byte aligned");
+    if (h->check) {
+        int crc = check_pattern(h, "ens_pcg_solve_ir", J, nnz, rowptr, colidx, (cudaStream_t)stream);
+        if (crc) return crc;
+    }
     Geo g = geometry(J, S);
     const size_t need = ir_layout(J, S, E, g, nullptr, nullptr);
     if (work_bytes < need)
@@ -1559,6 +1567,10 @@ extern "C" int ens_pcg_solve_static(ens_handle h, int J, int64_t nnz, int S, int
         return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: null pointer");
     if (((uintptr_t)vals | (uintptr_t)dinv | (uintptr_t)b | (uintptr_t)x) & 15)
         return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: arrays must be 16-byte aligned");
+    if (h && h->check) {  // h may be NULL here
+        int crc = check_pattern(h, "ens_pcg_solve_static", J, nnz, rowptr, colidx, (cudaStream_t)stream);
+        if (crc) return crc;
+    }
     Geo g = geometry(J, S);
     const size_t need = layout(J, S, E, g, nullptr, nullptr);
     if (need > kStaticScratchBytes)
@@ -1592,6 +1604,10 @@ extern "C" int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const in
     if (!rowptr || !colidx || !vals || !p || !q || !work) return set_error(h, ENS_EINVAL, "ens_spmv: null pointer");
     if (((uintptr_t)vals | (uintptr_t)p | (uintptr_t)q | (uintptr_t)work) & 15)
         return set_error(h, ENS_EINVAL, "ens_spmv: arrays must be 16-byte aligned");
+    if (h->check) {
+        int crc = check_pattern(h, "ens_spmv", J, nnz, rowptr, colidx, (cudaStream_t)stream);
+        if (crc) return crc;
+    }
     Geo g = geometry(J, S);
     const size_t need = layout(J, S, E, g, nullptr, nullptr);
     if (work_bytes < need) return set_error(h, ENS_ENOMEM, "ens_spmv: workspace too small");

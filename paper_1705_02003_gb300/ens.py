@@ -26,7 +26,7 @@ EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "e
            "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv",
            "ens_pcg_solve_static", "ens_pcg_ir_workspace_size", "ens_pcg_solve_ir",
            "ens_adjoint_workspace_size", "ens_adjoint_grad", "ens_param_indicator",
-           "ens_stream_workspace_size", "ens_solve_stream", "ens_pcg_branches")
+           "ens_stream_workspace_size", "ens_solve_stream", "ens_pcg_branches", "ens_check_pattern")
 
 _lib = None
 _lock = threading.Lock()
@@ -69,6 +69,7 @@ def _declare(L):
     L.ens_pattern.argtypes = [vp, c.POINTER(Problem), vp, vp, vp]
     L.ens_assemble.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, c.c_int, vp,
                                vp, vp]
+    L.ens_check_pattern.argtypes = [vp, c.c_int, c.c_int64, vp, vp, vp]
     L.ens_pcg_branches.argtypes = [vp, c.c_int]
     L.ens_pcg_branches.restype = c.c_int
     L.ens_pcg_workspace_size.argtypes = [c.c_int, c.c_int64, c.c_int, c.c_int]
@@ -200,6 +201,16 @@ def ens_assemble(h: Handle, prob: Problem, S: int, E: int, xi, rowptr, colidx, v
                              _ptr(colidx), _ptr(vals), int(vals.dtype == torch.float32), _ptr(dinv),
                              _ptr(b), _stream(stream))
     h.check(rc, "ens_assemble")
+
+
+def ens_check_pattern(h: Handle, J: int, nnz: int, rowptr, colidx, stream=None):
+    """Validate a CSR graph; raises EnsError naming the failed checks."""
+    _check_dtype(rowptr, torch.int32, "rowptr")
+    _check_dtype(colidx, torch.int32, "colidx")
+    if rowptr.numel() != J + 1 or colidx.numel() != nnz:
+        raise ValueError("rowptr must hold J + 1 and colidx nnz entries")
+    h.check(load().ens_check_pattern(h.ptr, int(J), int(nnz), _ptr(rowptr), _ptr(colidx), _stream(stream)),
+            "ens_check_pattern")
 
 
 def ens_pcg_branches(h: Handle, E: int) -> int:

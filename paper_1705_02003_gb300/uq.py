@@ -19,6 +19,8 @@ order; per level the host reads back only the G surpluses it refines on.
 """
 from __future__ import annotations
 
+import json
+
 import numpy as np
 import torch
 
@@ -172,30 +174,52 @@ class Adaptive:
                 n += 3 * max(1, int(it[e0 * S:e1 * S].max()))
         return n
 
-    def run(self, grouping: str = "sur", seed: int = 0, record_trips: bool = False):
+    def run(self, grouping: str = "sur", seed: int = 0, record_trips: bool = False,
+            stop_after: int | None = None, resume: dict | None = None):
+        """Run the loop.  stop_after = k returns after k refined levels with
+        done = False; resume = such a result (or load_run of a saved one)
+        continues from there exactly as an uninterrupted run would."""
         wl, S, dev = self.wl, self.S, self.dev
         N = wl.nparam
         self.launches = 0
         self.solve_sets = []
         self.call_events = []
-        lvl, idx = ens.ens_sg_initial(N, wl.init_level)
-        y = coords(lvl, idx)
-        lvl_d = torch.from_numpy(lvl).to(dev)
-        idx_d = torch.from_numpy(idx).to(dev)
-        y_d = torch.from_numpy(y).to(dev)
-        M0 = len(lvl)
-        order = torch.arange(M0, device=dev)
-        G, I = self._solve(y_d, order, 0)
-        # surpluses of the initial grid, one level at a time (Eq. hierSGint)
-        cG = level_surpluses(self.h, lvl, lvl_d, idx_d, y_d, G)
-        cI = level_surpluses(self.h, lvl, lvl_d, idx_d, y_d, I)
-        self.launches += 2 * len(np.unique(lvl.sum(axis=1)))
-        levels = [(0, M0)]
-        perms = [np.arange(M0, dtype=np.int32)]
-        preds = [np.zeros(M0)]
-        rng_seed = seed
-        first = 0
+        if resume is None:
+            lvl, idx = ens.ens_sg_initial(N, wl.init_level)
+            y = coords(lvl, idx)
+            lvl_d = torch.from_numpy(lvl).to(dev)
+            idx_d = torch.from_numpy(idx).to(dev)
+            y_d = torch.from_numpy(y).to(dev)
+            M0 = len(lvl)
+            order = torch.arange(M0, device=dev)
+            G, I = self._solve(y_d, order, 0)
+            # surpluses of the initial grid, one level at a time (Eq. hierSGint)
+            cG = level_surpluses(self.h, lvl, lvl_d, idx_d, y_d, G)
+            cI = level_surpluses(self.h, lvl, lvl_d, idx_d, y_d, I)
+            self.launches += 2 * len(np.unique(lvl.sum(axis=1)))
+            levels = [(0, M0)]
+            perms = [np.arange(M0, dtype=np.int32)]
+            preds = [np.zeros(M0)]
+            rng_seed = seed
+            first = 0
+        else:
+            if resume["done"] or resume["grouping"] != grouping or resume["S"] != S:
+                raise ValueError("resume needs an unfinished run of the same grouping and S")
+            lvl, idx = resume["lvl"], resume["idx"]
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+            lvl_d, idx_d, y_d = t(lvl), t(idx), t(resume["y"])
+            G, I, cG, cI = t(resume["G"]), t(resume["I"]), t(resume["cG"]), t(resume["cI"])
+            levels = [tuple(l) for l in resume["levels"]]
+            perms = list(resume["perms"])
+            preds = list(resume["preds"])
+            rng_seed = resume["rng_seed"]
+            first = levels[-1][0]
+        refined = 0
+        done = True
         while True:
+            if stop_after is not None and refined >= stop_after:
+                done = False
+                break
             cG_host = cG[first:].cpu().numpy()
             cG_all = np.concatenate([np.zeros(first), cG_host])
             nl, ni = ens.ens_sg_refine(lvl, idx, first, cG_all, wl.tau, wl.max_level)
@@ -240,9 +264,34 @@ class Adaptive:
             I = torch.cat([I, In])
             cG = torch.cat([cG, cGn])
             cI = torch.cat([cI, cIn])
+            refined += 1
         return dict(lvl=lvl, idx=idx, y=y_d.cpu().numpy(), G=G.cpu().numpy(), I=I.cpu().numpy(),
                     cG=cG.cpu().numpy(), cI=cI.cpu().numpy(), levels=levels, perms=perms, preds=preds,
-                    S=S)
+                    S=S, grouping=grouping, rng_seed=rng_seed, done=done)
+
+
+def save_run(run: dict, path: str) -> None:
+    """Write a run of Adaptive.run (finished or not) to an .npz checkpoint."""
+    arrays = {k: run[k] for k in ("lvl", "idx", "y", "G", "I", "cG", "cI")}
+    for j, (p, q) in enumerate(zip(run["perms"], run["preds"])):
+        arrays[f"perm{j}"] = p
+        arrays[f"pred{j}"] = q
+    meta = {"levels": [list(map(int, l)) for l in run["levels"]], "S": int(run["S"]),
+            "grouping": run["grouping"], "rng_seed": int(run["rng_seed"]), "done": bool(run["done"])}
+    np.savez(path, meta=np.array(json.dumps(meta)), **arrays)
+
+
+def load_run(path: str) -> dict:
+    """Read a checkpoint written by save_run."""
+    with np.load(path, allow_pickle=False) as z:
+        meta = json.loads(str(z["meta"]))
+        run = {k: z[k] for k in ("lvl", "idx", "y", "G", "I", "cG", "cI")}
+        n = len(meta["levels"])
+        run["perms"] = [z[f"perm{j}"] for j in range(n)]
+        run["preds"] = [z[f"pred{j}"] for j in range(n)]
+    run.update(levels=[tuple(l) for l in meta["levels"]], S=meta["S"], grouping=meta["grouping"],
+               rng_seed=meta["rng_seed"], done=meta["done"])
+    return run
 
 
 def ratios(run: dict, S: int | None = None):

@@ -88,3 +88,54 @@ def test_work_ratio_matches_oracle():
         it = rng.integers(1, 500, 77).astype(np.float64)
         p = rng.permutation(77).astype(np.int32)
         assert uq.work_ratio(S, p, it) == pytest.approx(O.work_ratio(S, p, it), rel=1e-14)
+
+
+def test_run_checkpoint_round_trip(tmp_path):
+    """save_run / load_run keep every array bit for bit and the loop metadata."""
+    from paper_1705_02003_gb300 import uq
+
+    rng = np.random.default_rng(0)
+    run = {"lvl": rng.integers(0, 4, (7, 2)).astype(np.int8), "idx": rng.integers(0, 9, (7, 2)).astype(np.int32),
+           "y": rng.uniform(-1, 1, (7, 2)), "G": rng.random(7), "I": rng.integers(1, 99, 7).astype(np.float64),
+           "cG": rng.standard_normal(7), "cI": rng.standard_normal(7), "levels": [(0, 4), (4, 7)],
+           "perms": [np.arange(4, dtype=np.int32), np.array([2, 0, 1], np.int32)],
+           "preds": [np.zeros(4), rng.random(3)], "S": 8, "grouping": "rand", "rng_seed": 5, "done": False}
+    path = str(tmp_path / "ck.npz")
+    uq.save_run(run, path)
+    back = uq.load_run(path)
+    for k in ("lvl", "idx", "y", "G", "I", "cG", "cI"):
+        assert back[k].dtype == run[k].dtype and np.array_equal(back[k], run[k])
+    for a, b in zip(back["perms"] + back["preds"], run["perms"] + run["preds"]):
+        assert np.array_equal(a, b)
+    assert back["levels"] == run["levels"] and back["S"] == 8 and back["grouping"] == "rand"
+    assert back["rng_seed"] == 5 and back["done"] is False
+
+
+def test_entry_points_refuse_null_arguments_without_crashing():
+    """Every entry point called with a NULL handle, NULL arrays and zero sizes
+    returns an error code (ens_pcg_branches returns 0 as documented); none
+    dereferences the handle or an array before checking it.  Runs on a machine
+    without a GPU: the argument checks come before any CUDA call."""
+    import ctypes as c
+
+    L = ens.load()
+    skip = {"ens_create", "ens_last_error", "ens_problem_size", "ens_pcg_workspace_size",
+            "ens_pcg_ir_workspace_size", "ens_stream_workspace_size", "ens_adjoint_workspace_size",
+            "ens_sg_refine", "ens_sg_initial"}
+    for name in ens.EXPORTS:
+        if name in skip:
+            continue
+        f = getattr(L, name)
+        args = []
+        for t in f.argtypes:
+            if t in (c.c_int, c.c_int64, c.c_size_t):
+                args.append(0)
+            elif t is c.c_double:
+                args.append(0.0)
+            else:
+                args.append(None)
+        rc = f(*args)
+        if name == "ens_pcg_branches":
+            assert rc == 0
+        else:
+            assert rc < 0, name

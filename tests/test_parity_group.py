@@ -176,3 +176,25 @@ def test_parameter_grouping_in_the_loop(h):
     for lev, (a, b) in enumerate(par["levels"]):
         if (b - a) % wl.S == 0:
             assert R["its"][0][lev] <= R["run"][0][lev] + 1e-12
+
+
+@pytest.mark.parametrize("grouping", ["sur", "rand"])
+def test_checkpoint_resume_equals_uninterrupted(h, tmp_path, grouping):
+    """A run stopped after one refined level, written to disk, read back and
+    resumed ends bit for bit where the uninterrupted run ends (the random
+    grouping also carries its seed over)."""
+    wl = inputs.WORKLOADS["fd5_32_adaptive"]
+    ad = uq.Adaptive(h, wl)
+    full = ad.run(grouping, seed=3)
+    part = ad.run(grouping, seed=3, stop_after=1)
+    assert full["done"] and not part["done"] and len(part["levels"]) == 2 < len(full["levels"])
+    path = str(tmp_path / "run.npz")
+    uq.save_run(part, path)
+    rest = ad.run(grouping, resume=uq.load_run(path))
+    assert rest["done"] and rest["levels"] == full["levels"]
+    for k in ("lvl", "idx", "y", "G", "I", "cG", "cI"):
+        assert np.array_equal(rest[k], full[k]), k
+    for a, b in zip(rest["perms"], full["perms"]):
+        assert np.array_equal(a, b)
+    with pytest.raises(ValueError):
+        ad.run("nat" if grouping != "nat" else "sur", resume=uq.load_run(path))

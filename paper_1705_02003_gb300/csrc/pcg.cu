@@ -389,7 +389,7 @@ constexpr int kChunk = 9;  // nonzeros loaded together per row (covers the 5/7/9
 // variant is a function of the pattern and S only, so the results still do not
 // depend on E, on lane position or on the other lanes.
 template <int S, int V_, int KC> struct SpmvOcc {
-    static constexpr int value = S == 1 ? 3 : (V_ == 1 ? 4 : 3);
+    static constexpr int value = S == 1 ? 3 : (S >= 64 ? 2 : (V_ == 1 ? 4 : 3));
 };
 
 template <typename T, int S, int V_, int KC>
@@ -618,7 +618,11 @@ __global__ void k_spmv_prep(Args a)
     if (L < a.E) a.w.ens_live[L] = a.S;
 }
 
-// The K2 variant for S and the pattern's mean row length (see k_spmv).
+// The K2 variant for S and the pattern's mean row length (see k_spmv): the
+// chunk matches the stencil (5, 7 or 9 nonzeros), because a chunk slot past the
+// end of a row is an FP64 multiply-add the whole warp skips but still issues
+// (measured on the 7-point rows with KC = 9: the FP64 pipe busy 27 % longer
+// than the real multiply-adds need).
 template <typename T, int S>
 void launch_k2(const Args &a, cudaStream_t st)
 {
@@ -626,13 +630,17 @@ void launch_k2(const Args &a, cudaStream_t st)
     const double row = (double)a.nnz / a.J;
     const T *vals = (const T *)a.vals, *p = (const T *)a.w.p;
     T *q = (T *)a.w.q;
-    if constexpr (sizeof(T) == 8 && (S == 16 || S == 32)) {
-        if (row <= 5.5) {
+    constexpr int V1 = SpmvGeo<S>::V;
+    if (row <= 5.5) {
+        if constexpr (sizeof(T) == 8 && (S == 16 || S == 32))
             k_spmv<T, S, 2, 5><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
-            return;
-        }
+        else
+            k_spmv<T, S, V1, 5><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
+    } else if (row <= 7.5) {
+        k_spmv<T, S, V1, 7><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
+    } else {
+        k_spmv<T, S, V1, 9><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
     }
-    k_spmv<T, S, SpmvGeo<S>::V, 9><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
 }
 
 template <typename T, int S>

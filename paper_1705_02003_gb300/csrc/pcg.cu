@@ -182,11 +182,12 @@ template <typename T, int V> struct Vec {
 };
 
 // V lanes per thread.  The vector kernels (K0, K3, K4) move 16 bytes per
-// access (two FP64 or four FP32 lanes); the SpMV (K2) takes one lane per
-// thread, which halves its registers and doubles its resident warps -- in FP64
-// it is bound by the FP64 issue rate, and more independent multiply-add
-// chains per SM keep that pipe busier (two lanes per thread are kept only for
-// S = 64, so a row stays within one warp).
+// access (two FP64 or four FP32 lanes); the SpMV (K2) by default takes one
+// lane per thread, which halves its registers and doubles its resident warps
+// -- in FP64 it is bound by the FP64 issue rate, and more independent
+// multiply-add chains per SM keep that pipe busier (S = 64 keeps two lanes
+// per thread so a row stays within one warp; see k_spmv for the 5-point
+// variant).
 template <int S, int V_> struct LaneGeo {
     static constexpr int V = V_;
     static constexpr int TPR = S / V;          // threads per row
@@ -377,17 +378,18 @@ __global__ void __launch_bounds__(kBlock) k_init(Args a, const double *__restric
 }
 
 // ---- K2: q = A p and p^T q per lane -> alpha -----------------------------------
-constexpr int kChunk = 9;  // nonzeros loaded together per row (covers the 5/7/9-point rows)
+constexpr int kChunk = 9;  // nonzeros loaded together per row in the refinement's FP64 residual
 
 // K2 variants: V_ lanes per thread, KC nonzeros of a row loaded at once (longer
-// rows continue chunk by chunk).  One lane per thread and KC = 9 suit the
-// 9-point rows, where the FP64 pipe is the limit and more warps keep it fed;
-// for short FP64 rows (the 5-point stencil, S of 16 or 32) two lanes per
-// thread put twice the bytes of a row in flight for the same column indices
-// (measured: 5-point 0.70 -> 0.45 ms per launch; for 7-point rows the variant
-// gained at large batches but lost with one or two ensembles, and in FP32).  The
-// variant is a function of the pattern and S only, so the results still do not
-// depend on E, on lane position or on the other lanes.
+// rows continue chunk by chunk; launch_k2 sizes KC to the stencil).  One lane
+// per thread suits the 7- and 9-point rows, where the FP64 pipe is the limit
+// and more warps keep it fed; for short FP64 rows (the 5-point stencil, S of 16
+// or 32) two lanes per thread put twice the bytes of a row in flight for the
+// same column indices (measured: 5-point 0.70 -> 0.45 ms per launch; for
+// 7-point rows two lanes gained at large batches but lost with one or two
+// ensembles, and in FP32).  The variant is a function of the pattern and S
+// only, so the results still do not depend on E, on lane position or on the
+// other lanes.
 template <int S, int V_, int KC> struct SpmvOcc {
     static constexpr int value = S == 1 ? 3 : (S >= 64 ? 2 : (V_ == 1 ? 4 : 3));
 };

@@ -255,7 +255,8 @@ def run_ours(args, wl):
             e1.record(stream)
             torch.cuda.synchronize()
             ta = e0.elapsed_time(e1) / 1e3
-            extra[arm] = {"value": M / ta, "R": ratios(r2)["run"][1]}
+            Ra = ratios(r2)["run"]
+            extra[arm] = {"value": M / ta, "R": Ra[1], "R_levels": Ra[0]}
         ps = Adaptive(h, wl, per_sample=True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -383,6 +384,8 @@ def run_ours(args, wl):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "R": {"sur": R["run"][1], "its": R["its"][1]},
+            "R_levels": {"sur": R["run"][0], "its": R["its"][0],
+                         "points": [b - a for a, b in run["levels"]]},
             "arms": extra,
             "level_calls": level_calls,
             "layers": layers,

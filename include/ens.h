@@ -78,9 +78,13 @@ typedef struct {
 typedef struct ens_ctx *ens_handle;
 
 /* Create a handle bound to CUDA device `device` (it becomes current for the
- * calling thread).  The handle owns a private capture stream and a cache of
- * instantiated CUDA graphs (keyed by every pointer and size of a solve); it is
- * not thread-safe.  ens_destroy releases both. */
+ * calling thread).  The handle owns a private capture stream, one device word
+ * for the graph check (ens_check_pattern) and a cache of at most 32
+ * instantiated CUDA graphs (keyed by every pointer and size of a solve, least
+ * recently used evicted first); it is not thread-safe.  ens_destroy releases
+ * all three.  Environment variables read here: ENS_PCG_HOST_LOOP,
+ * ENS_PCG_BRANCHES, ENS_CHECK (see ens_pcg_solve, ens_pcg_branches,
+ * ens_check_pattern). */
 int ens_create(ens_handle *h, int device);
 int ens_destroy(ens_handle h);
 /* (host) message of the last failed call on this handle; never NULL. */

@@ -268,6 +268,19 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         tp = e0.elapsed_time(e1) / 1e3
         extra["per_sample"] = {"value": M / tp, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r3["I"] - run["I"])))}
+        # the same surrogate groups, each level solved through the batching layer
+        # (live lanes of partly converged ensembles re-packed every 64 trips)
+        rp = Adaptive(h, wl, solver=ad.solver, repack=True)
+        rp.run("sur")  # warm-up
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r4 = rp.run("sur")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tr = e0.elapsed_time(e1) / 1e3
+        extra["sur_repack"] = {"value": M / tr, "same_grid": bool(np.array_equal(r4["lvl"], run["lvl"])),
+                               "same_iterations": bool(np.array_equal(r4["I"], run["I"]))}
+        del rp
 
     # per solve call (one per level): size, branches and time, from one more step
     ad.time_calls = True

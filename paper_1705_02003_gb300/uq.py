@@ -102,7 +102,8 @@ class Adaptive:
     """Runs the loop for one workload with one grouping."""
 
     def __init__(self, handle: ens.Handle, wl: inputs.Workload, S: int | None = None,
-                 solver: EnsembleSolver | None = None, per_sample: bool = False):
+                 solver: EnsembleSolver | None = None, per_sample: bool = False, repack: bool = False,
+                 chunk: int = 64):
         self.h = handle
         self.wl = wl
         self.S = wl.S if S is None else S
@@ -116,6 +117,12 @@ class Adaptive:
         self.dev = solver.dev
         self.launches = 0
         self.solve_sets = []
+        # repack: solve each level through the batching layer (ens_solve_stream),
+        # which gathers the live lanes of partly converged ensembles into fewer
+        # ensembles every `chunk` trips; the groups are still the grouping's.
+        self.repack = repack
+        self.chunk = chunk
+        self.stream_work = None
         self.sink = None  # optional callable(solver, M) run after every solve call
         self.time_calls = False  # record CUDA events around every ensemble solve call
         self.call_events = []
@@ -136,6 +143,18 @@ class Adaptive:
                 G[order[j:j + 1]] = q
                 I[order[j:j + 1]] = it.to(torch.float64)
                 self.solve_sets.append(np.array([offset + order_h[j]]))
+        elif self.repack:
+            from . import batching
+
+            E = -(-M // self.solver.S)
+            need = ens.ens_stream_workspace_size(self.prob, self.solver.S, E)
+            if self.stream_work is None or self.stream_work.numel() < need:
+                self.stream_work = torch.empty(need, dtype=torch.uint8, device=self.dev)
+            out = batching.solve_stream(self.h, self.prob, xi, self.solver.S, E, self.wl.rtol, self.wl.maxit,
+                                        chunk=self.chunk, work=self.stream_work)
+            G[order] = out["qoi"]
+            I[order] = out["iters"].to(torch.float64)
+            self.solve_sets.append(offset + order.cpu().numpy())
         else:
             if self.time_calls:
                 ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

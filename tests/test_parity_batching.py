@@ -72,3 +72,19 @@ def test_autotune_returns_a_candidate(h):
     xi = torch.from_numpy(inputs.draws(64, 6, seed=2)).cuda()
     best, times = batching.autotune(h, prob, xi, lanes=32, rtol=1e-8, maxit=20000, chunk=16)
     assert best in (8, 16, 32) and set(times) == {8, 16, 32}
+
+
+def test_adaptive_loop_with_repacked_levels_equals_fixed_levels(h):
+    """The flowchart loop with every level solved through the batching layer
+    (re-packing partly converged ensembles) visits the same grid with the same
+    iteration counts as the fixed-ensemble loop, and G agrees to rounding."""
+    from paper_1705_02003_gb300 import uq
+
+    wl = inputs.WORKLOADS["fd5_32_adaptive"]
+    fixed = uq.Adaptive(h, wl).run("sur")
+    rp = uq.Adaptive(h, wl, repack=True, chunk=8).run("sur")
+    assert np.array_equal(rp["lvl"], fixed["lvl"]) and np.array_equal(rp["idx"], fixed["idx"])
+    assert np.array_equal(rp["I"], fixed["I"])
+    np.testing.assert_allclose(rp["G"], fixed["G"], rtol=1e-12)
+    for a, b in zip(rp["perms"], fixed["perms"]):
+        assert np.array_equal(a, b)

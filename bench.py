@@ -578,14 +578,15 @@ def run_layers(h, stream):
         prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
         total = wl.samples if wl.samples else M
         xi = torch.from_numpy(inputs.draws(total, wl.nparam, seed=wl.seed)[:M]).cuda()
-        tune = {}
+        tune, ctune, chunk = {}, {}, 32
         if S is None:
             S, tune = batching.autotune(h, prob, xi, lanes=lanes, rtol=wl.rtol, maxit=wl.maxit, chunk=32,
                                         stream=stream)
+            chunk, ctune = batching.autotune_chunk(h, prob, xi, lanes, S, wl.rtol, wl.maxit, stream=stream)
         E = lanes // S
         work = torch.empty(ens.ens_stream_workspace_size(prob, S, E), dtype=torch.uint8, device="cuda")
-        batching.solve_stream(h, prob, xi[:lanes], S, E, wl.rtol, wl.maxit, chunk=32, work=work)  # warm-up
-        res, tstream = timed(lambda: batching.solve_stream(h, prob, xi, S, E, wl.rtol, wl.maxit, chunk=32,
+        batching.solve_stream(h, prob, xi[:lanes], S, E, wl.rtol, wl.maxit, chunk=chunk, work=work)  # warm-up
+        res, tstream = timed(lambda: batching.solve_stream(h, prob, xi, S, E, wl.rtol, wl.maxit, chunk=chunk,
                                                            work=work))
         del work
         fsol = EnsembleSolver(h, prob, S, lanes, wl.rtol, wl.maxit)
@@ -603,6 +604,7 @@ def run_layers(h, stream):
         torch.cuda.empty_cache()
         return {"workload": name, "sample": f"{M} uniform draws ({order_note}), {lanes} lanes", "S": S,
                 "S_autotuned": bool(tune), "autotune_seconds": {str(k): v for k, v in tune.items()},
+                "chunk": chunk, "chunk_autotune_seconds": {str(k): v for k, v in ctune.items()},
                 "stream_value": M / tstream, "fixed_batches_value": M / tfixed, "unit": "sample-solves/s",
                 "speedup": tfixed / tstream,
                 "iters_min_max": [int(res["iters"].min().item()), int(res["iters"].max().item())],

@@ -2,7 +2,8 @@
 
 ``solve_stream`` runs the continuous ensemble batching of ens_solve_stream
 (frozen lanes take the next queued sample; the drained pool is re-packed).
-``autotune`` picks the ensemble size S for a fixed lane capacity by timing
+``autotune`` picks the ensemble size S for a fixed lane capacity, and
+``autotune_chunk`` the trips per launch between harvests for that S, by timing
 each candidate on a bounded sample of the workload.
 """
 from __future__ import annotations
@@ -27,6 +28,19 @@ def solve_stream(h: ens.Handle, prob: ens.Problem, xi: torch.Tensor, S: int, E: 
     return dict(iters=iters, status=status, relres=relres, qoi=qoi)
 
 
+def _time_stream(h, prob, xi, S, E, rtol, maxit, chunk, stream):
+    work = torch.empty(ens.ens_stream_workspace_size(prob, S, E), dtype=torch.uint8, device=xi.device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    solve_stream(h, prob, xi, S, E, rtol, maxit, chunk=chunk, work=work, want_qoi=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    del work
+    return e0.elapsed_time(e1) / 1e3
+
+
 def autotune(h: ens.Handle, prob: ens.Problem, xi: torch.Tensor, lanes: int, rtol: float, maxit: int,
              chunk: int = 64, candidates=(8, 16, 32, 64), stream=None):
     """Time solve_stream on xi for each S with E = lanes / S; return (best S, {S: seconds})."""
@@ -35,16 +49,17 @@ def autotune(h: ens.Handle, prob: ens.Problem, xi: torch.Tensor, lanes: int, rto
     for S in candidates:
         if lanes % S:
             continue
-        E = lanes // S
-        work = torch.empty(ens.ens_stream_workspace_size(prob, S, E), dtype=torch.uint8, device=xi.device)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        solve_stream(h, prob, xi, S, E, rtol, maxit, chunk=chunk, work=work, want_qoi=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times[S] = e0.elapsed_time(e1) / 1e3
-        del work
+        times[S] = _time_stream(h, prob, xi, S, lanes // S, rtol, maxit, chunk, stream)
+    best = min(times, key=times.get)
+    return best, times
+
+
+def autotune_chunk(h: ens.Handle, prob: ens.Problem, xi: torch.Tensor, lanes: int, S: int, rtol: float,
+                   maxit: int, candidates=(16, 32, 64, 128), stream=None):
+    """The trips per launch between harvests and re-packs for a given S (any
+    chunk gives the same per-sample results; it trades host round trips
+    against lanes idling until the next harvest).  Returns (best, {chunk: s})."""
+    stream = torch.cuda.current_stream() if stream is None else stream
+    times = {c: _time_stream(h, prob, xi, S, lanes // S, rtol, maxit, c, stream) for c in candidates}
     best = min(times, key=times.get)
     return best, times

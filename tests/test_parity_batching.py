@@ -72,6 +72,8 @@ def test_autotune_returns_a_candidate(h):
     xi = torch.from_numpy(inputs.draws(64, 6, seed=2)).cuda()
     best, times = batching.autotune(h, prob, xi, lanes=32, rtol=1e-8, maxit=20000, chunk=16)
     assert best in (8, 16, 32) and set(times) == {8, 16, 32}
+    c, ct = batching.autotune_chunk(h, prob, xi, 32, best, 1e-8, 20000, candidates=(4, 16))
+    assert c in (4, 16) and set(ct) == {4, 16}
 
 
 def test_adaptive_loop_with_repacked_levels_equals_fixed_levels(h):

@@ -198,3 +198,27 @@ def test_checkpoint_resume_equals_uninterrupted(h, tmp_path, grouping):
         assert np.array_equal(a, b)
     with pytest.raises(ValueError):
         ad.run("nat" if grouping != "nat" else "sur", resume=uq.load_run(path))
+
+
+def test_empty_inputs_are_no_ops(h):
+    """Empty inputs at every step of the path: no points to group or sort, no
+    ensembles to solve, no samples to stream -- each returns without work."""
+    from paper_1705_02003_gb300 import batching
+    from paper_1705_02003_gb300.solver import EnsembleSolver
+
+    empty = torch.empty(0, dtype=torch.float64, device="cuda")
+    perm = torch.empty(0, dtype=torch.int32, device="cuda")
+    assert ens.ens_sort_chunk(h, empty, 8, perm) == 0
+    lvl, idx = ens.ens_sg_initial(2, 1)
+    cI = torch.zeros(len(lvl), dtype=torch.float64, device="cuda")
+    assert ens.ens_group(h, dev(lvl), dev(idx), cI, torch.empty(0, 2, dtype=torch.float64, device="cuda"), 8,
+                         empty, perm) == 0
+    prob = ens.problem("fd5", 8, 2, 3.0)
+    sol = EnsembleSolver(h, prob, 8, 8, 1e-8, 100)
+    it, st, rr, q = sol.solve(torch.empty(0, 2, dtype=torch.float64, device="cuda"))
+    assert it.numel() == st.numel() == rr.numel() == q.numel() == 0
+    J, nnz = sol.J, sol.nnz
+    ens.ens_pcg_solve(h, J, nnz, 8, 0, sol.rowptr, sol.colidx, sol.vals[:0], sol.dinv[:0], sol.b[:0], sol.x[:0],
+                      None, 1e-8, 100, sol.iters[:0], sol.relres[:0], sol.status[:0], sol.work)
+    out = batching.solve_stream(h, prob, torch.empty(0, 2, dtype=torch.float64, device="cuda"), 8, 1, 1e-8, 100)
+    assert out["iters"].numel() == 0

@@ -381,9 +381,11 @@ def run_ours(args, wl):
         threads = os.cpu_count() or 1
         pts = run["y"][:: max(1, M // args.cpu_samples)][: args.cpu_samples]
         rate, dt, _ = oracle_rate(wl, pts, threads)
+        rate1, dt1, _ = oracle_rate(wl, pts[:2], 1)  # the same solver on one core
         cpu = {"value": rate, "unit": "sample-solves/s", "cores": threads, "kind": "oracle",
                "sample": f"{len(pts)} of the {M} grid points (every {max(1, M // args.cpu_samples)}-th), "
-                         f"FP64 per-sample Jacobi-PCG, one sample per thread, {dt:.1f} s"}
+                         f"FP64 per-sample Jacobi-PCG, one sample per thread, {dt:.1f} s",
+               "single_core_value": rate1, "single_core_sample": f"the first 2 of those points, {dt1:.1f} s"}
 
     if rank == 0:
         line = {

@@ -215,6 +215,10 @@ def run_ours(args, wl):
     from paper_1705_02003_gb300.uq import Adaptive, ratios
 
     world, rank, local, pg = dist_setup(args)
+    if world > 1:
+        # N independent replicas: only the timed loop runs on every GPU; the
+        # single-GPU diagnostics (arms, layers, per-problem SpMV) are N = 1 work
+        args.no_arms = args.no_layers = True
     torch.cuda.set_device(local)
     h = ens.Handle(local)
     stream = torch.cuda.current_stream()

@@ -382,16 +382,16 @@ constexpr int kChunk = 9;  // nonzeros loaded together per row in the refinement
 
 // K2 variants: V_ lanes per thread, KC nonzeros of a row loaded at once (longer
 // rows continue chunk by chunk; launch_k2 sizes KC to the stencil).  One lane
-// per thread suits the 7- and 9-point rows, where the FP64 pipe is the limit
-// and more warps keep it fed; for short FP64 rows (the 5-point stencil, S of 16
-// or 32) two lanes per thread put twice the bytes of a row in flight for the
-// same column indices (measured: 5-point 0.70 -> 0.45 ms per launch; for
-// 7-point rows two lanes gained at large batches but lost with one or two
-// ensembles, and in FP32).  The variant is a function of the pattern and S
-// only, so the results still do not depend on E, on lane position or on the
-// other lanes.
+// per thread suits the 9-point rows, where the FP64 pipe is the limit and more
+// warps keep it fed; for shorter FP64 rows two lanes per thread put twice the
+// bytes of a row in flight for the same column indices (measured per launch:
+// 5-point rows at S = 16/32 0.70 -> 0.45 ms; 7-point rows at S = 32 0.64 ->
+// 0.61 ms with four ensembles and 1.36 -> 1.20 ms with one; at S = 16 and in
+// FP32 one lane per thread stayed faster).  The variant is a function of the
+// pattern, T and S only, so the results still do not depend on E, on lane
+// position or on the other lanes.
 template <int S, int V_, int KC> struct SpmvOcc {
-    static constexpr int value = S == 1 ? 3 : (S >= 64 ? 2 : (V_ == 1 ? 4 : 3));
+    static constexpr int value = S == 1 ? 3 : (S >= 64 ? 2 : (V_ == 1 ? 4 : (KC <= 5 ? 3 : 2)));
 };
 
 template <typename T, int S, int V_, int KC>
@@ -639,7 +639,10 @@ void launch_k2(const Args &a, cudaStream_t st)
         else
             k_spmv<T, S, V1, 5><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
     } else if (row <= 7.5) {
-        k_spmv<T, S, V1, 7><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
+        if constexpr (sizeof(T) == 8 && S == 32)
+            k_spmv<T, S, 2, 7><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
+        else
+            k_spmv<T, S, V1, 7><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
     } else {
         k_spmv<T, S, V1, 9><<<grid, kBlock, 0, st>>>(a, a.rowptr, a.colidx, vals, p, q);
     }

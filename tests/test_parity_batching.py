@@ -90,3 +90,21 @@ def test_adaptive_loop_with_repacked_levels_equals_fixed_levels(h):
     np.testing.assert_allclose(rp["G"], fixed["G"], rtol=1e-12)
     for a, b in zip(rp["perms"], fixed["perms"]):
         assert np.array_equal(a, b)
+
+
+def test_stream_full_batch_workload_sampled_against_oracle(h):
+    """The batching workload at full size: all 4096 draws of the 64^3 7-point
+    problem streamed through 64 lanes (S = 16, refills and re-packing), every
+    sample converged, and sampled samples against the oracle's own solves."""
+    wl = inputs.WORKLOADS["fd7_64_batch"]
+    prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    xi_h = inputs.draws(wl.samples, wl.nparam, seed=wl.seed)
+    out = batching.solve_stream(h, prob, torch.from_numpy(xi_h).cuda(), 16, 4, wl.rtol, wl.maxit, chunk=32)
+    it, st, rr, q = (out[k].cpu().numpy() for k in ("iters", "status", "relres", "qoi"))
+    assert np.all(st == ens.LANE_CONVERGED) and np.all(rr <= wl.rtol)
+    assert it.max() > 1.4 * it.min()  # uneven counts: the refills and re-packs really happened
+    pick = [0, 1234, 2047, 4095]
+    o = O.solve_batch(O.FD7_AXIS, wl.n, wl.nparam, wl.aniso, xi_h[pick], wl.rtol, wl.maxit,
+                      nthreads=os.cpu_count() or 4)
+    assert np.all(np.abs(it[pick] - o["iters"]) <= 1)
+    np.testing.assert_allclose(q[pick], o["G"], rtol=1e-9)

@@ -1,20 +1,34 @@
 """Benchmark: sample-solves/s of the surrogate-grouped ensemble PCG.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload q1_256_adaptive] [--no-arms]
+                    [--workload q1_256_adaptive] [--no-arms] [--no-layers] [--no-cpu]
+                    [--kernel-only [--kernel-ensembles E]]
 
 A step is one pass of the whole path over the workload: the grid-generation
 and grouping loop of the paper's flowchart (initial sparse grid, then per
 level: surrogate grouping (K6, K7), ensemble assembly (K1), ensemble Jacobi-PCG
 (K2-K4) to rel. residual 1e-8, QoI, surpluses and host refinement) until the
 sample budget is reached.  value = samples solved / device time (CUDA events
-around K steps, max over ranks).  The same run reports the natural-order and
-random groupings, one-sample-at-a-time PCG on the same GPU, the ensemble SpMV
-kernel against the HBM roofline, an end-to-end figure through the public API
-with host buffers, and the CPU oracle on a bounded sample of the same points.
+around K steps, max over ranks).
 
+The same run (one GPU) also reports:
+  arms            parameter-based, natural and random grouping; one sample at a
+                  time on the same GPU; the surrogate groups with lane re-packing
+  R, R_levels     the work ratio of Eq. (R) overall and per level
+  level_calls     each level's solve call: size, ensembles, branches, time
+  roofline        the ensemble SpMV (K2) against the FP64 and HBM roofs, and
+                  the whole path against its roofline
+  e2e             the same metric through the public API with host buffers
+  layers          FP32-in-FP64 refinement, batching (two iteration spreads),
+                  the adjoint gradient, each on a bounded sample
+  spmv_configs    K2 on the 7-point 64^3 / 128^3 and 5-point 512^2 problems
+  pilot_grouping  surrogate grouping of a non-adaptive sample set (Section 5)
+  cpu_baseline    the CPU oracle on a bounded sample of the same points
+
+--kernel-only times K2 alone (the case the Nsight Compute summaries use).
 --impl reference times the CPU oracle (the reference arm of this project) on
-the host cores for the same metric.  Multi-GPU runs are independent replicas.
+the host cores for the same metric.  Multi-GPU runs are independent replicas
+that time the loop only.
 """
 from __future__ import annotations
 

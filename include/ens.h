@@ -79,10 +79,11 @@ typedef struct ens_ctx *ens_handle;
 
 /* Create a handle bound to CUDA device `device` (it becomes current for the
  * calling thread).  The handle owns a private capture stream, one device word
- * for the graph check (ens_check_pattern) and a cache of at most 32
- * instantiated CUDA graphs (keyed by every pointer and size of a solve, least
- * recently used evicted first); it is not thread-safe.  ens_destroy releases
- * all three.  Environment variables read here: ENS_PCG_HOST_LOOP,
+ * for the graph check (ens_check_pattern), the scratch of the device-wide sort
+ * (allocated only when a grouping has more than 16384 points) and a cache of
+ * at most 32 instantiated CUDA graphs (keyed by every pointer and size of a
+ * solve, least recently used evicted first); it is not thread-safe.
+ * ens_destroy releases all of them.  Environment variables read here: ENS_PCG_HOST_LOOP,
  * ENS_PCG_BRANCHES, ENS_CHECK (see ens_pcg_solve, ens_pcg_branches,
  * ens_check_pattern). */
 int ens_create(ens_handle *h, int device);
@@ -270,7 +271,10 @@ int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const int32_t *rowp
  * returns perm[Mq], the stable ascending order of pred (ties keep index order),
  * which cut into consecutive runs of S forms the ensembles; *n_ens (host) =
  * ceil(Mq / S), the last ensemble padded.  M may be 0 (pred = 0, identity).
- * lvl[M][N] int8, idx[M][N] int32, surplus[M] f64: device.  Mq <= 16384. */
+ * lvl[M][N] int8, idx[M][N] int32, surplus[M] f64: device.  Mq <= 2^26.  Up to
+ * 16384 points the sort runs in one thread block; above that it runs over the
+ * whole GPU on scratch the handle owns, allocated (or grown) on first use,
+ * which synchronises `stream` once.  Both give the same permutation. */
 int ens_group(ens_handle h, int N, int M, const int8_t *lvl, const int32_t *idx,
               const double *surplus, int Mq, const double *yq, int S, double *pred,
               int32_t *perm, int *n_ens, void *stream);
@@ -294,7 +298,9 @@ int ens_qoi(ens_handle h, int J, int S, int E, const double *x, const double *w,
             void *stream);
 
 /* The sort-and-chunk step of ens_group alone, on caller keys[Mq] (device):
- * used for the natural (identity keys), random and iteration-sorted groupings. */
+ * used for the natural (identity keys), random and iteration-sorted groupings.
+ * Numbers ascend, NaN keys come last, ties keep index order; Mq <= 2^26, with
+ * the same one-block / device-wide split as ens_group. */
 int ens_sort_chunk(ens_handle h, int Mq, const double *keys, int S, int32_t *perm, int *n_ens,
                    void *stream);
 

@@ -55,6 +55,7 @@ extern "C" int ens_destroy(ens_handle h)
     }
     if (h->capture) cudaStreamDestroy(h->capture);
     if (h->check_flag) cudaFree(h->check_flag);
+    if (h->sort_scratch) cudaFree(h->sort_scratch);
     delete h;
     return ENS_OK;
 }

@@ -31,6 +31,8 @@ struct ens_ctx {
     int branches = 0;                        // ENS_PCG_BRANCHES=n: graph branches of a PCG loop (0: one per ensemble, at most 16)
     int check = 0;                           // ENS_CHECK=1: validate the caller's CSR graph before a solve
     int *check_flag = nullptr;               // device word for the graph check
+    void *sort_scratch = nullptr;            // device-wide sort of more than 16384 keys (grown on demand)
+    size_t sort_scratch_bytes = 0;
 };
 
 namespace ens {

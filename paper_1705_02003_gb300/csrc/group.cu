@@ -13,14 +13,21 @@
 // prediction is the same double a plain host loop gives.  Terms whose basis
 // value is zero are skipped (adding +-0 leaves a sum unchanged).
 //
-// K7 is a bitonic sort in one CTA over (key, index) pairs: the index breaks
-// ties, which makes the order total and therefore equal to a stable sort.
+// K7 is a bitonic sort over (key, index) pairs: the index breaks ties, which
+// makes the order total and therefore equal to a stable sort.  Up to 16384
+// keys it runs in one CTA in shared memory; beyond that the same network runs
+// over the whole GPU, one launch per compare-exchange stage, on scratch the
+// handle owns (the order of a total order is unique, so both give the same
+// permutation).
 #include "ens_common.cuh"
+
+#include <algorithm>
 
 namespace ens {
 namespace {
 
-constexpr int kMaxSort = 16384;
+constexpr int kMaxSort = 16384;           // one CTA
+constexpr int kMaxSortGlobal = 1 << 26;   // device-wide network
 
 __global__ void k_sg_eval(int N, int M, const int8_t *__restrict__ lvl, const int32_t *__restrict__ idx,
                           const double *__restrict__ surplus, int Mq, const double *__restrict__ yq,
@@ -92,8 +99,67 @@ __global__ void k_sort(int Mq, const double *__restrict__ keys, int32_t *__restr
     for (int t = threadIdx.x; t < Mq; t += blockDim.x) perm[t] = ix[t];
 }
 
+// Device-wide form: pairs in handle scratch, padded to a power of two with
+// NaN keys whose indices follow every real one (so they sort last).
+__global__ void k_sort_init(int Mq, int P, const double *__restrict__ keys, double *k, int *ix)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P; t += (long long)gridDim.x * blockDim.x) {
+        k[t] = t < Mq ? (keys ? keys[t] : 0.0) : __longlong_as_double(0x7ff8000000000000LL);
+        ix[t] = (int)t;
+    }
+}
+
+__global__ void k_sort_stage(int P, int size, int stride, double *k, int *ix)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P; t += (long long)gridDim.x * blockDim.x) {
+        const long long o = t ^ stride;
+        if (o <= t) continue;
+        const bool up = (t & size) == 0;
+        const double kt = k[t], ko = k[o];
+        const int it = ix[t], io = ix[o];
+        if (up ? before(ko, io, kt, it) : before(kt, it, ko, io)) {
+            k[t] = ko;
+            k[o] = kt;
+            ix[t] = io;
+            ix[o] = it;
+        }
+    }
+}
+
+__global__ void k_sort_out(int Mq, const int *__restrict__ ix, int32_t *__restrict__ perm)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Mq; t += (long long)gridDim.x * blockDim.x)
+        perm[t] = ix[t];
+}
+
+int sort_global(ens_ctx *h, int Mq, const double *keys, int32_t *perm, cudaStream_t st)
+{
+    int P = 1;
+    while (P < Mq) P <<= 1;
+    const size_t need = (size_t)P * (sizeof(double) + sizeof(int));
+    if (h->sort_scratch_bytes < need) {
+        // grow the handle's scratch; the old buffer may still be read by queued work
+        ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+        if (h->sort_scratch) cudaFree(h->sort_scratch);
+        h->sort_scratch = nullptr;
+        h->sort_scratch_bytes = 0;
+        ENS_CUDA_CHECK(h, cudaMalloc(&h->sort_scratch, need));
+        h->sort_scratch_bytes = need;
+    }
+    double *k = (double *)h->sort_scratch;
+    int *ix = (int *)(k + P);
+    const int grid = (int)std::min<long long>(((long long)P + 255) / 256, 152LL * 16);
+    k_sort_init<<<grid, 256, 0, st>>>(Mq, P, keys, k, ix);
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) k_sort_stage<<<grid, 256, 0, st>>>(P, size, stride, k, ix);
+    k_sort_out<<<grid, 256, 0, st>>>(Mq, ix, perm);
+    ENS_LAUNCH_CHECK(h, "device-wide sort");
+    return ENS_OK;
+}
+
 int sort_launch(ens_ctx *h, int Mq, const double *keys, int32_t *perm, cudaStream_t st)
 {
+    if (Mq > kMaxSort) return sort_global(h, Mq, keys, perm, st);
     int P = 1;
     while (P < Mq) P <<= 1;
     if (P < 2) P = 2;
@@ -115,7 +181,7 @@ extern "C" int ens_sort_chunk(ens_handle h, int Mq, const double *keys, int S, i
 {
     if (!h) return ENS_EINVAL;
     if (S < 1) return set_error(h, ENS_EINVAL, "ens_sort_chunk: S < 1");
-    if (Mq < 0 || Mq > kMaxSort) return set_error(h, ENS_EINVAL, "ens_sort_chunk: Mq out of range (0..16384)");
+    if (Mq < 0 || Mq > kMaxSortGlobal) return set_error(h, ENS_EINVAL, "ens_sort_chunk: Mq out of range (0..2^26)");
     if (n_ens) *n_ens = (Mq + S - 1) / S;
     if (Mq == 0) return ENS_OK;
     if (!perm) return set_error(h, ENS_EINVAL, "ens_sort_chunk: null perm");
@@ -128,7 +194,7 @@ extern "C" int ens_group(ens_handle h, int N, int M, const int8_t *lvl, const in
 {
     if (!h) return ENS_EINVAL;
     if (N < 1 || N > 16) return set_error(h, ENS_EINVAL, "ens_group: N must be in 1..16");
-    if (M < 0 || Mq < 0 || Mq > kMaxSort) return set_error(h, ENS_EINVAL, "ens_group: bad M / Mq (Mq <= 16384)");
+    if (M < 0 || Mq < 0 || Mq > kMaxSortGlobal) return set_error(h, ENS_EINVAL, "ens_group: bad M / Mq (Mq <= 2^26)");
     if (S < 1) return set_error(h, ENS_EINVAL, "ens_group: S < 1");
     if (n_ens) *n_ens = (Mq + S - 1) / S;
     if (Mq == 0) return ENS_OK;

@@ -156,18 +156,25 @@ class Adaptive:
             I[order] = out["iters"].to(torch.float64)
             self.solve_sets.append(offset + order.cpu().numpy())
         else:
-            if self.time_calls:
-                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                ev[0].record()
-            it, st, rr, q = self.solver.solve(xi)
-            if self.time_calls:
-                ev[1].record()
-                self.call_events.append((M, ev))
-            if self.sink:
-                self.sink(self.solver, M)
-            G[order] = q
-            I[order] = it.to(torch.float64)
-            self.solve_sets.append(offset + order.cpu().numpy())
+            # a level larger than the solver's capacity is solved in calls of
+            # whole ensembles (capacity is a multiple of S), which leaves every
+            # ensemble -- and so every sample's result -- as in one call
+            cap = self.solver.Emax * self.solver.S
+            order_h = order.cpu().numpy()
+            for a0 in range(0, M, cap):
+                a1 = min(M, a0 + cap)
+                if self.time_calls:
+                    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                    ev[0].record()
+                it, st, rr, q = self.solver.solve(xi[a0:a1])
+                if self.time_calls:
+                    ev[1].record()
+                    self.call_events.append((a1 - a0, ev))
+                if self.sink:
+                    self.sink(self.solver, a1 - a0)
+                G[order[a0:a1]] = q
+                I[order[a0:a1]] = it.to(torch.float64)
+                self.solve_sets.append(offset + order_h[a0:a1])
         return G, I
 
     def call_times(self):

@@ -235,3 +235,21 @@ def test_empty_inputs_are_no_ops(h):
                       None, 1e-8, 100, sol.iters[:0], sol.relres[:0], sol.status[:0], sol.work)
     out = batching.solve_stream(h, prob, torch.empty(0, 2, dtype=torch.float64, device="cuda"), 8, 1, 1e-8, 100)
     assert out["iters"].numel() == 0
+
+
+def test_levels_larger_than_the_solver_are_solved_in_whole_ensembles(h):
+    """A solver that holds one ensemble at a time runs every level in calls of
+    whole ensembles; the loop's results equal the one-call run bit for bit."""
+    from paper_1705_02003_gb300.solver import EnsembleSolver
+
+    wl = inputs.WORKLOADS["fd5_32_adaptive"]
+    full = uq.Adaptive(h, wl).run("sur")
+    prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    small = uq.Adaptive(h, wl, solver=EnsembleSolver(h, prob, wl.S, wl.S, wl.rtol, wl.maxit))
+    part = small.run("sur")
+    assert max(b - a for a, b in full["levels"]) > wl.S  # some level really needed several calls
+    assert len(small.solve_sets) > len(full["levels"])
+    for k in ("lvl", "idx", "G", "I", "cG", "cI"):
+        assert np.array_equal(part[k], full[k]), k
+    for a, b in zip(part["perms"], full["perms"]):
+        assert np.array_equal(a, b)

@@ -27,6 +27,8 @@ _SRC = ["problem.c", "pcg.c", "sgrid.c"]
 FD5_LOGKL = 1
 Q1_ROT = 2
 FD7_AXIS = 3
+Q1_3D_KL = 4      # Section 4, Test 1 (3-D trilinear FEM, exponential-covariance KL field)
+Q1_3D_DISC = 5    # Section 4, Test 2 (the same with the discontinuous ahat(xi))
 
 CONVERGED, MAXIT, BREAKDOWN, BADINPUT = 0, 1, 2, 3
 
@@ -74,6 +76,11 @@ def _declare(L):
     L.or_tensor.argtypes = [c.c_int, c.c_int, c.c_double, _f64p, _f64p, _f64p]
     L.or_param_indicator.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, _f64p]
     L.or_param_indicator.restype = c.c_double
+    L.or_kl_1d.argtypes = [c.c_int, c.POINTER(c.c_double), c.POINTER(c.c_double)]
+    L.or_kl_lambda.argtypes = [c.c_int]
+    L.or_kl_lambda.restype = c.c_double
+    L.or_kl_mode.argtypes = [c.c_int, _f64p]
+    L.or_kl_mode.restype = c.c_double
     L.or_spmv.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, _f64p]
     L.or_spmv.restype = None
     L.or_jacobi.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p]
@@ -142,11 +149,30 @@ def assemble(kind: int, n: int, nparam: int, aniso: float, xi, rowptr=None, coli
 
 
 def tensor(kind: int, nparam: int, aniso: float, xi, x):
-    d = 3 if kind == FD7_AXIS else 2
+    d = 3 if kind in (FD7_AXIS, Q1_3D_KL, Q1_3D_DISC) else 2
     K = np.zeros(d * d, np.float64)
     if lib().or_tensor(kind, nparam, float(aniso), _f64(xi), _f64(x), K):
         raise ValueError("tensor failed")
     return K.reshape(d, d)
+
+
+def kl_1d(which: int):
+    """(w, lambda) of the first even (0) or odd (1) 1-D exponential-kernel mode."""
+    w = ctypes.c_double()
+    lam = ctypes.c_double()
+    if lib().or_kl_1d(int(which), ctypes.byref(w), ctypes.byref(lam)):
+        raise ValueError("which must be 0 or 1")
+    return w.value, lam.value
+
+
+def kl_lambda(k: int) -> float:
+    """3-D covariance eigenvalue of parameter k = 1..4 (sigma0 included)."""
+    return lib().or_kl_lambda(int(k))
+
+
+def kl_mode(k: int, x) -> float:
+    """3-D KL mode b_k(x) of parameter k = 1..4 at x in [0, 1]^3."""
+    return lib().or_kl_mode(int(k), _f64(x))
 
 
 def param_indicator(kind: int, n: int, nparam: int, aniso: float, xi) -> float:

@@ -24,6 +24,14 @@
  *   OR_FD7_AXIS    3-D 7-point finite differences,
  *                  A = diag(1, 10^(aniso xi_1), 10^(aniso xi_2)) exp(0.3 sum_{k=3}^{6} xi_k phi_k),
  *                  f = 1.  N = 6.
+ *   OR_Q1_3D_KL    3-D trilinear (Q1) finite elements on (n+1)^3 cells, 27-point
+ *                  stencil, the field of Section 4 (Test 1):
+ *                  A = diag(a, 1, 1), a = a_min + ahat exp(sum_{k=1}^{4} sqrt(lambda_k) b_k(x) xi_k)
+ *                  (Eq. diff-coeff), (lambda_k, b_k) the four largest eigenpairs of the
+ *                  exponential covariance sigma0 exp(-||x - x'||_1 / delta), delta = 1/4,
+ *                  sigma0 = sqrt(300); ahat = 1, a_min = 0.1.  f = 1.  N = 4.
+ *   OR_Q1_3D_DISC  the same with Test 2's discontinuous ahat(xi) = 1, 100, 10 for
+ *                  r < d/4, d/4 <= r < d/2, r >= d/2 (r = ||xi||_2, d = sqrt(3)).
  * phi_k are products of sines sin(m pi x_d); the mode lists are in problem.c.
  * The log-coefficient form follows Eq. (diff-coeff); the tensor forms are the
  * anisotropic A(x, y) of Section 2.1 / Section 4.
@@ -37,7 +45,7 @@
 extern "C" {
 #endif
 
-enum { OR_FD5_LOGKL = 1, OR_Q1_ROT = 2, OR_FD7_AXIS = 3 };
+enum { OR_FD5_LOGKL = 1, OR_Q1_ROT = 2, OR_FD7_AXIS = 3, OR_Q1_3D_KL = 4, OR_Q1_3D_DISC = 5 };
 
 /* Per-sample PCG outcome codes. */
 enum { OR_CONVERGED = 0, OR_MAXIT = 1, OR_BREAKDOWN = 2, OR_BADINPUT = 3 };
@@ -54,6 +62,13 @@ int  or_assemble(int kind, int n, int nparam, double aniso, const double *xi,
 int  or_tensor(int kind, int nparam, double aniso, const double *xi,
                const double *x, double *K);
 double or_param_indicator(int kind, int n, int nparam, double aniso, const double *xi);
+/* The exponential-covariance KL eigenpairs of OR_Q1_3D_*: the 1-D root w and
+ * eigenvalue of the first even (which = 0) or odd (which = 1) mode of
+ * exp(-|s - t| / delta) on [0, 1]; the 3-D eigenvalue lambda_k and mode b_k(x)
+ * of parameter k = 1..4 (covariance scale sigma0 included). */
+int    or_kl_1d(int which, double *w, double *lambda);
+double or_kl_lambda(int k);
+double or_kl_mode(int k, const double *x);
 
 /* ---- pcg.c -------------------------------------------------------------- */
 void or_spmv(int J, const int64_t *rowptr, const int32_t *colidx,

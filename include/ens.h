@@ -40,7 +40,7 @@ enum {
     ENS_ECUDA = -2,    /* a CUDA runtime error; message in ens_last_error */
     ENS_ENOMEM = -3,   /* caller workspace smaller than the *_workspace_size answer */
     ENS_ETIMEOUT = -4, /* a bounded device-side wait gave up */
-    ENS_ENOTSUP = -5   /* combination not implemented (e.g. adjoint of the Q1 problem) */
+    ENS_ENOTSUP = -5   /* combination not implemented (e.g. adjoint of a finite-element problem) */
 };
 
 /* Per-sample ("lane") outcome of a solve. */
@@ -65,11 +65,20 @@ enum {
  *                  N = 4.  Tensor at element centroids, exact element stiffness.
  *   ENS_FD7_AXIS   3-D 7-point FD, A = diag(1, 10^(aniso xi_1), 10^(aniso xi_2))
  *                  exp(0.3 sum_{k=3}^{6} xi_k phi_k), phi = sin(a pi x) sin(b pi y) sin(c pi z),
- *                  (a,b,c) = (1,1,1), (2,1,1), (1,2,1), (1,1,2); f = 1; N = 6. */
-enum { ENS_FD5_LOGKL = 1, ENS_Q1_ROT = 2, ENS_FD7_AXIS = 3 };
+ *                  (a,b,c) = (1,1,1), (2,1,1), (1,2,1), (1,1,2); f = 1; N = 6.
+ *   ENS_Q1_3D_KL   the problem of Section 4, Test 1: 3-D trilinear FEM (27-point) on
+ *                  (n+1)^3 cells, A = diag(a, 1, 1) at element centroids,
+ *                  a = 0.1 + exp(sum_{k=1}^{4} sqrt(lambda_k) b_k(x) xi_k) (Eq. diff-coeff),
+ *                  (lambda_k, b_k) the four largest eigenpairs of the exponential
+ *                  covariance sqrt(300) exp(-||x - x'||_1 / (1/4)) on [0,1]^3 (products of
+ *                  the first even 1-D mode e and odd mode o: eee, oee, eoe, eeo);
+ *                  f = 1 (b = h^3); N = 4; aniso unused.
+ *   ENS_Q1_3D_DISC Section 4, Test 2: the same with ahat(xi) exp(...) in place of
+ *                  exp(...), ahat = 1, 100, 10 for ||xi||_2 < sqrt(3)/4, < sqrt(3)/2, >=. */
+enum { ENS_FD5_LOGKL = 1, ENS_Q1_ROT = 2, ENS_FD7_AXIS = 3, ENS_Q1_3D_KL = 4, ENS_Q1_3D_DISC = 5 };
 
 typedef struct {
-    int kind;     /* ENS_FD5_LOGKL | ENS_Q1_ROT | ENS_FD7_AXIS */
+    int kind;     /* ENS_FD5_LOGKL | ENS_Q1_ROT | ENS_FD7_AXIS | ENS_Q1_3D_KL | ENS_Q1_3D_DISC */
     int n;        /* interior nodes per axis, >= 2 */
     int nparam;   /* N, random parameters per sample */
     double aniso; /* exponent scale of the axis anisotropy */
@@ -194,7 +203,7 @@ size_t ens_adjoint_workspace_size(const ens_problem *p, int S, int E);
  * A(xi) lam = w (A is symmetric; b does not depend on xi), writes
  *   grad[E][S][nparam] = dQ/dxi = -lam^T (dA/dxi) u,   Q = w^T u,
  * summed face by face over the FD operator (FD5 and FD7 problems only;
- * ENS_ENOTSUP for Q1).  xi[E][S][nparam] as for ens_assemble.  Deterministic:
+ * ENS_ENOTSUP for the finite-element problems).  xi[E][S][nparam] as for ens_assemble.  Deterministic:
  * fixed per-lane summation order. */
 int ens_adjoint_grad(ens_handle h, const ens_problem *p, int S, int E, const double *xi,
                      const double *u, const double *lam, double *grad, void *work,

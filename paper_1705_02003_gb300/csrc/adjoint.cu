@@ -168,8 +168,8 @@ extern "C" int ens_adjoint_grad(ens_handle h, const ens_problem *p, int S, int E
     std::string why;
     int rc = problem_check(p, &J, &nnz, &why);
     if (rc) return set_error(h, rc, "ens_adjoint_grad: " + why);
-    if (p->kind == ENS_Q1_ROT)
-        return set_error(h, ENS_ENOTSUP, "ens_adjoint_grad: the Q1 problem has no adjoint gradient here");
+    if (p->kind != ENS_FD5_LOGKL && p->kind != ENS_FD7_AXIS)
+        return set_error(h, ENS_ENOTSUP, "ens_adjoint_grad: only the FD problems have an adjoint gradient here");
     if (!lane_count_ok(S) || E < 0 || E > 65535) return set_error(h, ENS_EINVAL, "ens_adjoint_grad: bad S / E");
     if (E == 0) return ENS_OK;
     if (!xi || !u || !lam || !grad || !work) return set_error(h, ENS_EINVAL, "ens_adjoint_grad: null pointer");

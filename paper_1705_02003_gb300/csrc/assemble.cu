@@ -13,9 +13,16 @@
 //       elements shared by the two nodes in lexicographic element order; f = 1
 //       gives b = h^2.
 //
+//   Q1 3-D (27-point, Section 4): element stiffness of the diagonal tensor
+//       diag(a, 1, 1) at the element centroid, summed over the (up to) eight
+//       elements shared by the two nodes; f = 1 gives b = h^3.
+//
 // One thread per (ensemble, row, lane); lanes are fastest so every store of a
 // nonzero's S values is one contiguous run.
 #include "ens_common.cuh"
+
+#include <cmath>
+#include <mutex>
 
 namespace ens {
 
@@ -32,7 +39,7 @@ __global__ void k_rowptr(int kind, int n, int J, int32_t *rowptr)
     int t = threadIdx.x;
     int chunk = (J + blockDim.x - 1) / blockDim.x;
     int r0 = t * chunk, r1 = min(J, r0 + chunk);
-    int cols[9];
+    int cols[27];
     long long s = 0;
     for (int r = r0; r < r1; r++) s += row_neighbours(kind, n, r, cols);
     part[t] = s;
@@ -59,7 +66,7 @@ __global__ void k_colidx(int kind, int n, int J, const int32_t *__restrict__ row
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= J) return;
-    int cols[9];
+    int cols[27];
     int c = row_neighbours(kind, n, r, cols);
     int32_t k0 = rowptr[r];
     for (int q = 0; q < c; q++) colidx[k0 + q] = cols[q];
@@ -276,6 +283,136 @@ __global__ void k_assemble_q1(int n, double aniso, int S, int E, const double *_
     }
 }
 
+// ---- Section 4 field: exponential-covariance KL, Test 1 / Test 2 ---------------
+// The covariance sigma0 exp(-||x - x'||_1 / delta) (delta = 1/4, sigma0 =
+// sqrt(300)) is a product of 1-D kernels exp(-|s - t| / delta) on [0, 1].  With
+// u = s - 1/2 and c = 1/delta the 1-D eigenfunctions are cos(w u) (w tan(w/2) = c)
+// and sin(w u) (c tan(w/2) + w = 0), eigenvalue 2c / (w^2 + c^2), squared L2 norm
+// 1/2 + sin(w) / (2w) and 1/2 - sin(w) / (2w).  The four largest 3-D products are
+// e e e, o e e, e o e, e e o with e, o the first even and odd modes.
+struct KLField {
+    double we, wo;  // first even / odd roots
+    double ie, io;  // 1 / L2 norm of cos(we u), sin(wo u)
+    double sl[4];   // sqrt(lambda_k) of the four 3-D modes, sigma0 included
+};
+
+// Root of an increasing function on (lo, hi), halving until the bracket stops shrinking.
+template <class F> double bisect(F f, double lo, double hi)
+{
+    for (;;) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) return mid;
+        if (f(mid) < 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+}
+
+const KLField &kl_field()
+{
+    static KLField k;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const double c = 4.0, pi = 3.14159265358979323846;  // c = 1 / delta
+        k.we = bisect([c](double w) { return w * std::tan(0.5 * w) - c; }, 0.0, pi);
+        k.wo = bisect([c](double w) { return c * std::tan(0.5 * w) + w; }, pi, 2.0 * pi);
+        k.ie = 1.0 / std::sqrt(0.5 + std::sin(k.we) / (2.0 * k.we));
+        k.io = 1.0 / std::sqrt(0.5 - std::sin(k.wo) / (2.0 * k.wo));
+        const double le = 2.0 * c / (k.we * k.we + c * c), lo = 2.0 * c / (k.wo * k.wo + c * c);
+        const double sigma0 = std::sqrt(300.0);
+        k.sl[0] = std::sqrt(sigma0 * le * le * le);
+        for (int q = 1; q < 4; q++) k.sl[q] = std::sqrt(sigma0 * lo * le * le);
+    });
+    return k;
+}
+
+// ahat(xi) of Test 2 (1 for Test 1); r = ||xi||_2 summed left to right.
+__device__ __forceinline__ double q13_ahat(int kind, const double *y)
+{
+    if (kind != ENS_Q1_3D_DISC) return 1.0;
+    const double r = sqrt(dadd(dadd(dadd(dmul(y[0], y[0]), dmul(y[1], y[1])), dmul(y[2], y[2])), dmul(y[3], y[3])));
+    const double d = sqrt(3.0);
+    return r < d / 4.0 ? 1.0 : (r < d / 2.0 ? 100.0 : 10.0);
+}
+
+// a(x, xi) at a point: 0.1 + ahat exp(sum_k sqrt(lambda_k) b_k(x) xi_k).
+__device__ __forceinline__ double q13_a(const KLField &f, const double *y, double ahat, double x0, double x1,
+                                        double x2)
+{
+    const double e0 = f.ie * cos(f.we * (x0 - 0.5)), o0 = f.io * sin(f.wo * (x0 - 0.5));
+    const double e1 = f.ie * cos(f.we * (x1 - 0.5)), o1 = f.io * sin(f.wo * (x1 - 0.5));
+    const double e2 = f.ie * cos(f.we * (x2 - 0.5)), o2 = f.io * sin(f.wo * (x2 - 0.5));
+    double s = f.sl[0] * (e0 * e1 * e2) * y[0];
+    s += f.sl[1] * (o0 * e1 * e2) * y[1];
+    s += f.sl[2] * (e0 * o1 * e2) * y[2];
+    s += f.sl[3] * (e0 * e1 * o2) * y[3];
+    return 0.1 + ahat * exp(s);
+}
+
+template <typename V>
+__global__ void k_assemble_q13(int n, int kind, KLField f, int S, int E, const double *__restrict__ xi,
+                               const int32_t *__restrict__ rowptr, V *__restrict__ vals, double *__restrict__ dinv,
+                               double *__restrict__ b, long long nnz, const int32_t *__restrict__ lanes, int nlanes)
+{
+    const int n2 = n * n, J = n2 * n;
+    const long long total = lanes ? (long long)nlanes * J : (long long)E * J * S;
+    const double h = 1.0 / (double)(n + 1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int s, row, e;
+        if (lanes) {
+            const int L = lanes[t / J];
+            row = (int)(t % J);
+            e = L / S;
+            s = L % S;
+        } else {
+            s = (int)(t % S);
+            long long er = t / S;
+            row = (int)(er % J);
+            e = (int)(er / J);
+        }
+        const double *xs = xi + ((long long)e * S + s) * 4;
+        const double y[4] = {xs[0], xs[1], xs[2], xs[3]};
+        const double ahat = q13_ahat(kind, y);
+        const int i = row % n, j = (row / n) % n, l = row / n2;
+        // the eight elements around node (i+1, j+1, l+1), lower corners (i + qx, j + qy, l + qz)
+        double a[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int ex = i + (q & 1), ey = j + ((q >> 1) & 1), ez = l + (q >> 2);
+            a[q] = q13_a(f, y, ahat, ((double)ex + 0.5) * h, ((double)ey + 0.5) * h, ((double)ez + 0.5) * h);
+        }
+        const long long base = (long long)e * nnz * S + s;
+        long long k = rowptr[row];
+        double dv = 1.0;
+        for (int dl = -1; dl <= 1; dl++)
+            for (int dj = -1; dj <= 1; dj++)
+                for (int di = -1; di <= 1; di++) {
+                    const int ii = i + di, jj = j + dj, ll = l + dl;
+                    if (ii < 0 || ii >= n || jj < 0 || jj >= n || ll < 0 || ll >= n) continue;
+                    double v = 0.0;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int ex = i + (q & 1), ey = j + ((q >> 1) & 1), ez = l + (q >> 2);
+                        // local coordinates (0/1) of the row node and the column node in the element
+                        const int aR = (i + 1) - ex, bR = (j + 1) - ey, cR = (l + 1) - ez;
+                        const int aC = (ii + 1) - ex, bC = (jj + 1) - ey, cC = (ll + 1) - ez;
+                        if (aC < 0 || aC > 1 || bC < 0 || bC > 1 || cC < 0 || cC > 1) continue;
+                        const double dx = q1_sign(aR) * q1_sign(aC) * q1_mass(bR, bC) * q1_mass(cR, cC);
+                        const double dy = q1_mass(aR, aC) * q1_sign(bR) * q1_sign(bC) * q1_mass(cR, cC);
+                        const double dz = q1_mass(aR, aC) * q1_mass(bR, bC) * q1_sign(cR) * q1_sign(cC);
+                        v += h * (a[q] * dx + dy + dz);
+                    }
+                    if (di == 0 && dj == 0 && dl == 0) dv = v;
+                    put(vals, base + (k++) * S, v);
+                }
+        const long long vi = ((long long)e * J + row) * S + s;
+        if (dinv) dinv[vi] = 1.0 / dv;
+        if (b) b[vi] = h * h * h;
+    }
+}
+
 // ---- parameter-based grouping indicator (Section 3.2, Eq. pb-indicator) -------
 // H(xi) = max over the points where the tensor is evaluated (FD face
 // midpoints, Q1 element centroids) of lambda_max(A) / lambda_min(A).  The
@@ -287,7 +424,7 @@ __device__ __forceinline__ void hmax(double *H, double v)
 }
 
 __global__ void k_indicator(int kind, int n, int N, double aniso, int M, const double *__restrict__ xi_all,
-                            double *__restrict__ H)
+                            double *__restrict__ H, KLField f)
 {
     const int m = blockIdx.y;
     const double *xs = xi_all + (size_t)m * N;
@@ -295,7 +432,17 @@ __global__ void k_indicator(int kind, int n, int N, double aniso, int M, const d
     for (int k = 0; k < N; k++) x[k] = xs[k];
     const double den = (double)(n + 1);
     double best = 0.0;
-    if (kind == ENS_Q1_ROT) {
+    if (kind == ENS_Q1_3D_KL || kind == ENS_Q1_3D_DISC) {
+        // element centroids; diag(a, 1, 1) has eigenvalues a, 1, 1
+        const int m1 = n + 1, ne = m1 * m1 * m1;
+        const double ahat = q13_ahat(kind, x);
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ne; q += gridDim.x * blockDim.x) {
+            const int ex = q % m1, ey = (q / m1) % m1, ez = q / (m1 * m1);
+            const double a = q13_a(f, x, ahat, ((double)ex + 0.5) / den, ((double)ey + 0.5) / den,
+                                   ((double)ez + 0.5) / den);
+            best = fmax(best, a > 1.0 ? a : 1.0 / a);
+        }
+    } else if (kind == ENS_Q1_ROT) {
         const int ne = (n + 1) * (n + 1);
         const double th = dmul(0.25, dadd(1.0, x[2]));
         const double c = cospi(th), sn = sinpi(th);
@@ -378,6 +525,13 @@ int problem_check(const ens_problem *p, int *J, int64_t *nnz, std::string *why)
         *J = (int)(n * n * n);
         *nnz = 7 * n * n * n - 6 * n * n;
         break;
+    case ENS_Q1_3D_KL:
+    case ENS_Q1_3D_DISC:
+        if (p->nparam != 4) { *why = "3-D Q1 problem needs nparam == 4"; return ENS_EINVAL; }
+        if (n > 400) { *why = "n too large"; return ENS_EINVAL; }
+        *J = (int)(n * n * n);
+        *nnz = (3 * n - 2) * (3 * n - 2) * (3 * n - 2);
+        break;
     default:
         *why = "unknown problem kind";
         return ENS_EINVAL;
@@ -441,6 +595,13 @@ int assemble_lanes(ens_ctx *h, const ens_problem *p, int S, int E, const double 
         else
             k_assemble_q1<double><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lanes, nlanes);
         break;
+    case ENS_Q1_3D_KL:
+    case ENS_Q1_3D_DISC:
+        if (vals_f32)
+            k_assemble_q13<float><<<grid, 256, 0, st>>>(p->n, p->kind, kl_field(), S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lanes, nlanes);
+        else
+            k_assemble_q13<double><<<grid, 256, 0, st>>>(p->n, p->kind, kl_field(), S, E, xi, rowptr, (double *)vals, dinv, b, nnz, lanes, nlanes);
+        break;
     default:
         if (vals_f32)
             k_assemble_fd7<float><<<grid, 256, 0, st>>>(p->n, p->aniso, S, E, xi, rowptr, (float *)vals, dinv, b, nnz, lanes, nlanes);
@@ -498,11 +659,13 @@ extern "C" int ens_param_indicator(ens_handle h, const ens_problem *p, int M, co
     if (!xi || !H) return set_error(h, ENS_EINVAL, "ens_param_indicator: null pointer");
     cudaStream_t st = (cudaStream_t)stream;
     ENS_CUDA_CHECK(h, cudaMemsetAsync(H, 0, (size_t)M * sizeof(double), st));
-    const long long pts = p->kind == ENS_Q1_ROT ? (long long)(p->n + 1) * (p->n + 1) : (long long)J;
+    const long long m1 = p->n + 1;
+    const long long pts = p->kind == ENS_Q1_ROT ? m1 * m1
+                          : (p->kind == ENS_Q1_3D_KL || p->kind == ENS_Q1_3D_DISC ? m1 * m1 * m1 : (long long)J);
     unsigned bx = (unsigned)((pts + 255) / 256);
     if (bx > 64) bx = 64;
     dim3 grid(bx, M);
-    k_indicator<<<grid, 256, 0, st>>>(p->kind, p->n, p->nparam, p->aniso, M, xi, H);
+    k_indicator<<<grid, 256, 0, st>>>(p->kind, p->n, p->nparam, p->aniso, M, xi, H, kl_field());
     ENS_LAUNCH_CHECK(h, "ens_param_indicator");
     return ENS_OK;
 }

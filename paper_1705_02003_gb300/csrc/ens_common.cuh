@@ -78,6 +78,7 @@ __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 
 // Neighbours of `row` in increasing column order; returns the count (<= 9).
+// cols must hold 27 entries (the 3-D trilinear stencil).
 __device__ __host__ inline int row_neighbours(int kind, int n, int row, int *cols)
 {
     int c = 0;
@@ -95,6 +96,15 @@ __device__ __host__ inline int row_neighbours(int kind, int n, int row, int *col
                 int ii = i + di, jj = j + dj;
                 if (ii >= 0 && ii < n && jj >= 0 && jj < n) cols[c++] = ii + n * jj;
             }
+    } else if (kind == ENS_Q1_3D_KL || kind == ENS_Q1_3D_DISC) {
+        int n2 = n * n;
+        int i = row % n, j = (row / n) % n, l = row / n2;
+        for (int dl = -1; dl <= 1; dl++)
+            for (int dj = -1; dj <= 1; dj++)
+                for (int di = -1; di <= 1; di++) {
+                    int ii = i + di, jj = j + dj, ll = l + dl;
+                    if (ii >= 0 && ii < n && jj >= 0 && jj < n && ll >= 0 && ll < n) cols[c++] = ii + n * jj + n2 * ll;
+                }
     } else {
         int n2 = n * n;
         int i = row % n, j = (row / n) % n, l = row / n2;

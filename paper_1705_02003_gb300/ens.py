@@ -15,8 +15,8 @@ import torch
 
 from . import build as _build
 
-FD5_LOGKL, Q1_ROT, FD7_AXIS = 1, 2, 3
-KINDS = {"fd5": FD5_LOGKL, "q1": Q1_ROT, "fd7": FD7_AXIS}
+FD5_LOGKL, Q1_ROT, FD7_AXIS, Q1_3D_KL, Q1_3D_DISC = 1, 2, 3, 4, 5
+KINDS = {"fd5": FD5_LOGKL, "q1": Q1_ROT, "fd7": FD7_AXIS, "q1_3d_kl": Q1_3D_KL, "q1_3d_disc": Q1_3D_DISC}
 
 OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5
 LANE_CONVERGED, LANE_MAXIT, LANE_BREAKDOWN, LANE_BADINPUT, LANE_INACTIVE = 0, 1, 2, 3, 4

@@ -16,6 +16,10 @@ Section 4, which used no public dataset):
                     1024 uniform draws, S = 32, FP32-in-FP64 refinement
   fd5_512_adjoint   2-D 5-point FD, 512 x 512, N = 8, 1024 uniform draws,
                     S = 32, QoI = mean of u over [0.4, 0.6]^2
+  q1_32c_test1      the paper's own problem (Section 4, Test 1): 3-D trilinear FEM on
+                    32^3 cells, exponential-covariance KL field, N = 4, adaptive
+                    sparse grid from level 1, tau = 1e-3, N_max = 2000, rtol 1e-7, S = 16
+  q1_32c_test2      the same with Test 2's discontinuous coefficient
 """
 from __future__ import annotations
 
@@ -51,6 +55,10 @@ WORKLOADS = {
     "fd7_64_batch": Workload("fd7_64_batch", "fd7", 64, 6, 3.0, 32, 1e-8, 50000, samples=4096),
     "fd7_128_mixed": Workload("fd7_128_mixed", "fd7", 128, 6, 2.0, 32, 1e-10, 50000, samples=1024),
     "fd5_512_adjoint": Workload("fd5_512_adjoint", "fd5", 512, 8, 3.0, 32, 1e-8, 50000, samples=1024),
+    "q1_32c_test1": Workload("q1_32c_test1", "q1_3d_kl", 31, 4, 0.0, 16, 1e-7, 50000,
+                             tau=1e-3, init_level=1, n_max=2000),
+    "q1_32c_test2": Workload("q1_32c_test2", "q1_3d_disc", 31, 4, 0.0, 16, 1e-7, 50000,
+                             tau=1e-3, init_level=1, n_max=2000),
 }
 
 

@@ -8,7 +8,8 @@ import torch
 import oracle as O
 from paper_1705_02003_gb300 import ens
 
-OKIND = {"fd5": O.FD5_LOGKL, "q1": O.Q1_ROT, "fd7": O.FD7_AXIS}
+OKIND = {"fd5": O.FD5_LOGKL, "q1": O.Q1_ROT, "fd7": O.FD7_AXIS, "q1_3d_kl": O.Q1_3D_KL,
+         "q1_3d_disc": O.Q1_3D_DISC}
 
 
 class Case:

@@ -47,7 +47,8 @@ def test_create_without_gpu_fails_cleanly():
 @pytest.mark.parametrize("wl", list(inputs.WORKLOADS.values()), ids=lambda w: w.name)
 def test_problem_sizes_match_oracle(wl):
     p = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
-    kind = {"fd5": O.FD5_LOGKL, "q1": O.Q1_ROT, "fd7": O.FD7_AXIS}[wl.kind]
+    kind = {"fd5": O.FD5_LOGKL, "q1": O.Q1_ROT, "fd7": O.FD7_AXIS, "q1_3d_kl": O.Q1_3D_KL,
+            "q1_3d_disc": O.Q1_3D_DISC}[wl.kind]
     assert ens.ens_problem_size(p) == O.problem_size(kind, wl.n)
 
 

@@ -268,13 +268,23 @@ __device__ bool reduce_lanes(double (&acc)[NS][LG::V], double *part_base[NS], in
         }
     }
     __syncthreads();
+    {
+        // The G group sums of a lane are combined pairwise, group g with
+        // g + st for st = G/2, ..., 1: a fixed order with log2 G dependent
+        // additions.  (One thread adding the G sums in turn cost about 50 ns
+        // per addition at S = 1, where G = 256.)
+        const int g = tid / S, s = tid % S;
+        for (int st = LG::G / 2; st > 0; st >>= 1) {
+            if (g < st) {
+#pragma unroll
+                for (int ns = 0; ns < NS; ns++) grp[g][ns][s] = dadd(grp[g][ns][s], grp[g + st][ns][s]);
+            }
+            __syncthreads();
+        }
+    }
     if (tid < S) {
 #pragma unroll
-        for (int ns = 0; ns < NS; ns++) {
-            double v = 0.0;
-            for (int g = 0; g < LG::G; g++) v = dadd(v, grp[g][ns][tid]);
-            tot[ns * S + tid] = v;
-        }
+        for (int ns = 0; ns < NS; ns++) tot[ns * S + tid] = grp[0][ns][tid];
     }
     if (tid == 0) *counter = 0;
     __syncthreads();
@@ -1643,7 +1653,8 @@ extern "C" int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const in
 
 // ---- per-sample quantity of interest ---------------------------------------------
 // One block per ensemble; thread t owns lane t % S and rows t / S, t / S + 1024 / S, ...
-// so the per-lane sum has a fixed order (rows in stride, then the threads of a lane).
+// so the per-lane sum has a fixed order (rows in stride, then the threads of a lane
+// pairwise: thread group g with g + st for st = G/2, ..., 1).
 namespace ens {
 namespace {
 __global__ void __launch_bounds__(1024) k_qoi(int J, int S, const double *__restrict__ x,
@@ -1660,11 +1671,11 @@ __global__ void __launch_bounds__(1024) k_qoi(int J, int S, const double *__rest
     }
     sh[t] = acc;
     __syncthreads();
-    if (t < S) {
-        double v = 0.0;
-        for (int q = 0; q < G; q++) v = dadd(v, sh[q * S + t]);
-        out[(size_t)e * S + t] = v;
+    for (int st = G / 2; st > 0; st >>= 1) {
+        if (g < st) sh[t] = dadd(sh[t], sh[t + st * S]);
+        __syncthreads();
     }
+    if (t < S) out[(size_t)e * S + t] = sh[t];
 }
 }  // namespace
 }  // namespace ens

@@ -137,7 +137,7 @@ class Adaptive:
         if self.per_sample:
             order_h = order.cpu().numpy()
             for j in range(M):
-                it, st, rr, q = self.solver.solve(xi[j:j + 1])
+                it, st, rr, q = self._call(xi[j:j + 1])
                 if self.sink:
                     self.sink(self.solver, 1)
                 G[order[j:j + 1]] = q
@@ -163,19 +163,24 @@ class Adaptive:
             order_h = order.cpu().numpy()
             for a0 in range(0, M, cap):
                 a1 = min(M, a0 + cap)
-                if self.time_calls:
-                    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                    ev[0].record()
-                it, st, rr, q = self.solver.solve(xi[a0:a1])
-                if self.time_calls:
-                    ev[1].record()
-                    self.call_events.append((a1 - a0, ev))
+                it, st, rr, q = self._call(xi[a0:a1])
                 if self.sink:
                     self.sink(self.solver, a1 - a0)
                 G[order[a0:a1]] = q
                 I[order[a0:a1]] = it.to(torch.float64)
                 self.solve_sets.append(offset + order_h[a0:a1])
         return G, I
+
+    def _call(self, xs: torch.Tensor):
+        """One solve call, bracketed by CUDA events when time_calls is set."""
+        if not self.time_calls:
+            return self.solver.solve(xs)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        out = self.solver.solve(xs)
+        ev[1].record()
+        self.call_events.append((xs.shape[0], ev))
+        return out
 
     def call_times(self):
         """(M, milliseconds) of every ensemble solve call of the last run made

@@ -93,11 +93,12 @@ def test_adjoint_full_size_sampled_lane(h):
     assert np.all(np.abs(g[5] - go) <= 1e-6 * np.maximum(1e-3, np.abs(go))), (g[5], go)
 
 
-def test_q1_has_no_adjoint(h):
-    p = ens.problem("q1", 8, 4, 4.0)
+@pytest.mark.parametrize("kind,aniso", [("q1", 4.0), ("q1_3d_kl", 0.0), ("q1_3d_disc", 0.0)])
+def test_fem_problems_have_no_adjoint(h, kind, aniso):
+    p = ens.problem(kind, 8, 4, aniso)
     J, _ = ens.ens_problem_size(p)
     z = torch.zeros(J * 2, dtype=torch.float64, device="cuda")
     work = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
-    with pytest.raises(ens.EnsError, match="Q1"):
+    with pytest.raises(ens.EnsError, match="only the FD problems"):
         ens.ens_adjoint_grad(h, p, 2, 1, torch.zeros(8, dtype=torch.float64, device="cuda"), z, z,
                              torch.zeros(8, dtype=torch.float64, device="cuda"), work)

@@ -60,7 +60,7 @@ FP64_PEAK_SOURCE = "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 T
 
 # DRAM bytes of one K2 launch measured by ncu on the E = 8 case of the same
 # kernel (profiles/k_spmv_q1_256_E8.md), scaled by the units a launch processes.
-SPMV_TRAFFIC_PER_ENSEMBLE = {"q1_256_adaptive": (673.465856e6 + 37.092608e6) / 8}
+SPMV_TRAFFIC_PER_ENSEMBLE = {"q1_256_adaptive": (673.661696e6 + 37.994240e6) / 8}
 
 
 def spmv_traffic(wl, E):

@@ -22,7 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "liboracle.so")
-_SRC = ["problem.c", "pcg.c", "sgrid.c"]
+_SRC = ["problem.c", "pcg.c", "sgrid.c", "mg.c"]
 
 FD5_LOGKL = 1
 Q1_ROT = 2
@@ -86,6 +86,20 @@ def _declare(L):
     L.or_jacobi.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p]
     L.or_pcg.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_int, _f64p,
                          c.POINTER(c.c_int), c.POINTER(c.c_double)]
+    L.or_mg_levels.argtypes = [c.c_int, _i32p]
+    L.or_mg_galerkin.argtypes = [c.c_int, _i64p, _i32p, _f64p, c.c_int, _i64p, _i32p, _f64p]
+    L.or_mg_prolong.argtypes = [c.c_int, c.c_int, _f64p, _f64p]
+    L.or_mg_prolong.restype = None
+    L.or_mg_restrict.argtypes = [c.c_int, c.c_int, _f64p, _f64p]
+    L.or_mg_restrict.restype = None
+    L.or_gershgorin.argtypes = [c.c_int, _i64p, _i32p, _f64p]
+    L.or_gershgorin.restype = c.c_double
+    L.or_cheb.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, _f64p, _f64p]
+    L.or_cheb.restype = None
+    L.or_mg_coarse.argtypes = [c.c_int, _i64p, _i32p, _f64p, c.c_int, _f64p, c.POINTER(c.c_double)]
+    L.or_mg_apply.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, _f64p]
+    L.or_mgpcg.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_int, _f64p,
+                           c.POINTER(c.c_int), c.POINTER(c.c_double)]
     L.or_solve_batch.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, c.c_int, _f64p, c.c_double,
                                  c.c_int, c.c_int, _i32p, _i32p, _f64p, _f64p, c.c_void_p]
     L.or_pcg_ir.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_double, c.c_int,
@@ -207,6 +221,104 @@ def pcg(rowptr, colidx, vals, b, rtol: float, maxit: int):
     st = lib().or_pcg(J, rowptr, colidx, _f64(vals), _f64(b), float(rtol), int(maxit), x,
                       ctypes.byref(it), ctypes.byref(rr))
     return x, it.value, st, rr.value
+
+
+# ---- multigrid V-cycle preconditioner of the trilinear problems (mg.c) ----
+
+def mg_levels(n: int):
+    """Interior nodes per axis of each level: [n, (n-1)/2, ..., 3]."""
+    ns = np.zeros(8, np.int32)
+    L = lib().or_mg_levels(int(n), ns)
+    if L < 1:
+        raise ValueError(f"no multigrid hierarchy for n = {n} (n = 2^k - 1, k >= 2)")
+    return [int(v) for v in ns[:L]]
+
+
+def mg_galerkin(nf: int, rpf, cif, vf, nc: int):
+    """P^T A P of a fine 27-point matrix, in the coarse level's pattern."""
+    rpc, cic = pattern(Q1_3D_KL, nc)
+    vc = np.zeros(len(cic), np.float64)
+    if lib().or_mg_galerkin(int(nf), rpf, cif, _f64(vf), int(nc), rpc, cic, vc):
+        raise ValueError("bad levels or pattern")
+    return vc
+
+
+def mg_prolong(nf: int, nc: int, ec):
+    ef = np.zeros(nf ** 3, np.float64)
+    lib().or_mg_prolong(int(nf), int(nc), _f64(ec), ef)
+    return ef
+
+
+def mg_restrict(nf: int, nc: int, rf):
+    rc = np.zeros(nc ** 3, np.float64)
+    lib().or_mg_restrict(int(nf), int(nc), _f64(rf), rc)
+    return rc
+
+
+def gershgorin(rowptr, colidx, vals) -> float:
+    return lib().or_gershgorin(len(rowptr) - 1, rowptr, colidx, _f64(vals))
+
+
+def cheb(rowptr, colidx, vals, dinv, lmax: float, b, x):
+    """Degree-2 Chebyshev smoothing of A x = b from x (returns the new x)."""
+    x = _f64(x).copy()
+    lib().or_cheb(len(rowptr) - 1, rowptr, colidx, _f64(vals), _f64(dinv), float(lmax), _f64(b), x)
+    return x
+
+
+def mg_coarse(n: int, rowptr, colidx, vals, level: int):
+    """(values, Gershgorin bound) of level `level` of the hierarchy."""
+    nl = mg_levels(n)[level]
+    _, nnz = problem_size(Q1_3D_KL, nl)
+    vc = np.zeros(nnz, np.float64)
+    lm = ctypes.c_double()
+    if lib().or_mg_coarse(int(n), rowptr, colidx, _f64(vals), int(level), vc, ctypes.byref(lm)):
+        raise ValueError("hierarchy setup failed")
+    return vc, lm.value
+
+
+def mg_apply(n: int, rowptr, colidx, vals, r):
+    """z = one V-cycle applied to r."""
+    z = np.zeros(n ** 3, np.float64)
+    if lib().or_mg_apply(int(n), rowptr, colidx, _f64(vals), _f64(r), z):
+        raise ValueError("hierarchy setup failed")
+    return z
+
+
+def mgpcg(n: int, rowptr, colidx, vals, b, rtol: float, maxit: int):
+    """CG preconditioned by one V-cycle per iteration. Returns (x, iters, status, relres)."""
+    x = np.zeros(n ** 3, np.float64)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().or_mgpcg(int(n), rowptr, colidx, _f64(vals), _f64(b), float(rtol), int(maxit), x,
+                        ctypes.byref(it), ctypes.byref(rr))
+    return x, it.value, st, rr.value
+
+
+def solve_batch_mg(kind: int, n: int, nparam: int, aniso: float, xi, rtol: float, maxit: int,
+                   nthreads: int = 1, want_x: bool = False):
+    """solve_batch with the multigrid preconditioner (one sample per task)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    xi = _f64(xi)
+    M = xi.shape[0]
+    rp, ci = pattern(kind, n)
+
+    def one(m):
+        vals, b = assemble(kind, n, nparam, aniso, xi[m], rp, ci)
+        x, it, st, rr = mgpcg(n, rp, ci, vals, b, rtol, maxit)
+        return x, it, st, rr, float(np.dot(x, x))
+
+    if nthreads > 1:
+        with ThreadPoolExecutor(nthreads) as ex:
+            res = list(ex.map(one, range(M)))
+    else:
+        res = [one(m) for m in range(M)]
+    out = dict(iters=np.array([r[1] for r in res], np.int32), status=np.array([r[2] for r in res], np.int32),
+               relres=np.array([r[3] for r in res]), G=np.array([r[4] for r in res]))
+    if want_x:
+        out["x"] = np.array([r[0] for r in res])
+    return out
 
 
 def solve_batch(kind: int, n: int, nparam: int, aniso: float, xi, rtol: float, maxit: int,

@@ -70,6 +70,33 @@ int    or_kl_1d(int which, double *w, double *lambda);
 double or_kl_lambda(int k);
 double or_kl_mode(int k, const double *x);
 
+/* ---- mg.c: multigrid V-cycle preconditioner of the trilinear problems ---- */
+#define OR_MG_MAXLEV 8
+/* Levels of the hierarchy for n interior nodes per axis (n = 2^k - 1, k >= 2):
+ * writes ns[0..L-1] (n, (n-1)/2, ..., 3) and returns L, or -1. */
+int    or_mg_levels(int n, int *ns);
+/* A_c = P^T A_f P in the 27-point pattern of the coarse level (nf = 2 nc + 1). */
+int    or_mg_galerkin(int nf, const int64_t *rpf, const int32_t *cif, const double *vf,
+                      int nc, const int64_t *rpc, const int32_t *cic, double *vc);
+void   or_mg_prolong(int nf, int nc, const double *ec, double *ef);   /* ef = P ec */
+void   or_mg_restrict(int nf, int nc, const double *rf, double *rc);  /* rc = P^T rf */
+/* Gershgorin bound max_i sum_j |a_ij| / a_ii of D^-1 A; NaN if a row's ratio
+ * is not finite and positive. */
+double or_gershgorin(int J, const int64_t *rp, const int32_t *ci, const double *v);
+/* Degree-2 Chebyshev smoothing of A x = b from the x given, on [lmax/30, lmax]. */
+void   or_cheb(int J, const int64_t *rp, const int32_t *ci, const double *v, const double *dinv,
+               double lmax, const double *b, double *x);
+/* Level `level`'s Galerkin values and Gershgorin bound of the hierarchy built
+ * from the fine matrix (n per axis, the OR_Q1_3D pattern). */
+int    or_mg_coarse(int n, const int64_t *rp, const int32_t *ci, const double *v, int level,
+                    double *vc, double *lmax);
+/* z = one V-cycle applied to r. */
+int    or_mg_apply(int n, const int64_t *rp, const int32_t *ci, const double *v, const double *r,
+                   double *z);
+/* CG preconditioned by one V-cycle per iteration; conventions of or_pcg. */
+int    or_mgpcg(int n, const int64_t *rp, const int32_t *ci, const double *v, const double *b,
+                double rtol, int maxit, double *x, int *iters, double *relres);
+
 /* ---- pcg.c -------------------------------------------------------------- */
 void or_spmv(int J, const int64_t *rowptr, const int32_t *colidx,
              const double *vals, const double *x, double *y);

@@ -23,8 +23,9 @@ The same run (one GPU) also reports:
                   the adjoint gradient, each on a bounded sample
   spmv_configs    K2 on the 7-point 64^3 / 128^3 and 5-point 512^2 problems
   pilot_grouping  surrogate grouping of a non-adaptive sample set (Section 5)
-  paper_tables    Section 4's Test 1 / Test 2 (32^3 trilinear FEM, N = 4):
-                  R_l, R, measured and predicted speed-up for S = 4..32
+  paper_tables    Section 4's Test 1 / Test 2 (32^3 trilinear FEM, N = 4), with
+                  the Jacobi and the multigrid preconditioner: R_l, R,
+                  measured and predicted speed-up for S = 4..32
   cpu_baseline    the CPU oracle on a bounded sample of the same points
 
 --kernel-only times K2 alone (the case the Nsight Compute summaries use).
@@ -528,8 +529,9 @@ def run_pilot(h, stream):
 def run_paper(h, stream, S_list=(4, 8, 16, 32)):
     """Section 4's Tables 2 and 3 on the GPU path.  For Test 1 and Test 2
     (32^3 trilinear FEM, N = 4, adaptive grid from level 1, tau = 1e-3,
-    N_max = 2000, Jacobi-PCG to a relative residual of 1e-7): R_l per level
-    and R (Eqs. Rl and R) of the surrogate (sur), parameter (par),
+    N_max = 2000, CG to a relative residual of 1e-7), each with the Jacobi
+    preconditioner and with the multigrid V-cycle (ens_mgpcg_solve): R_l per
+    level and R (Eqs. Rl and R) of the surrogate (sur), parameter (par),
     generation-order (nat) and iteration-sorted (its) groupings at S = 4..32;
     the measured speed-up = the time of all solve calls made one sample at a
     time / the time of all ensemble solve calls; and the predicted speed-up =
@@ -547,55 +549,58 @@ def run_paper(h, stream, S_list=(4, 8, 16, 32)):
     out = {}
     for name in ("q1_32c_test1", "q1_32c_test2"):
         wl = inputs.WORKLOADS[name]
-        seq = Adaptive(h, wl, per_sample=True)
-        y0 = torch.zeros(1, wl.nparam, dtype=torch.float64, device="cuda")
-        seq.solver.solve(y0)  # warm-up (graph instantiation)
-        seq.time_calls = True
-        r0 = seq.run("nat")
-        t_seq = solve_ms(seq)
-        # the equal-iteration case uses the sample of median iteration count,
-        # so that its fixed per-call cost weighs as in a typical solve
-        j_med = int(np.argsort(r0["I"], kind="stable")[len(r0["I"]) // 2])
-        y_med = torch.from_numpy(r0["y"][j_med:j_med + 1].copy()).to("cuda")
-        seq.call_events = []
-        for _ in range(5):
-            seq._call(y_med)
-        t1 = float(np.median([ms for _, ms in seq.call_times()]))
-        del seq
-        res = {"points": len(r0["I"]), "levels": [b - a for a, b in r0["levels"]],
-               "iters_min": int(r0["I"].min()), "iters_max": int(r0["I"].max()),
-               "iters_mean": float(r0["I"].mean()), "sequential_solve_ms": t_seq,
-               "sigma_sample_iters": int(r0["I"][j_med]), "sigma_one_solve_ms": t1, "S": {}}
-        for S in S_list:
-            ad = Adaptive(h, wl, S=S)
-            ad.run("nat")  # warm-up: instantiates every level's loop graph
-            Ms = min(512, ad.solver.Emax * S)
-            ys = y_med.expand(Ms, -1).contiguous()
-            ad.solver.solve(ys)
-            ad.time_calls = True
-            ad.call_events = []
-            ad._call(ys)
-            sigma = Ms * t1 / ad.call_times()[0][1]
-            row = {"sigma": sigma}
-            same_grid = True
-            for g in ("sur", "par", "nat"):
-                r = ad.run(g)
-                t = solve_ms(ad)
-                same_grid &= bool(np.array_equal(r["lvl"], r0["lvl"]))
-                R = ratios(r)
-                row[g] = {"R_levels": R["run"][0], "R": R["run"][1], "speedup": t_seq / t,
-                          "pred_speedup": sigma / R["run"][1], "solve_ms": t}
-                if g == "sur":
-                    row["its"] = {"R_levels": R["its"][0], "R": R["its"][1], "pred_speedup": sigma / R["its"][1]}
-                    row["sur_pred_rel_err"] = [
-                        float(np.mean(np.abs(pr - r["I"][a:b])) / np.mean(r["I"][a:b]))
-                        for (a, b), pr in list(zip(r["levels"], r["preds"]))[1:]]
-                    row["max_iter_diff_vs_sequential"] = int(np.max(np.abs(r["I"] - r0["I"])))
-            row["same_grid_as_sequential"] = same_grid
-            res["S"][S] = row
-            del ad
-            torch.cuda.empty_cache()
-        out[name] = res
+        out[name] = {}
+        for pc in ("jacobi", "mg"):
+            seq = Adaptive(h, wl, per_sample=True, precond=pc)
+            y0 = torch.zeros(1, wl.nparam, dtype=torch.float64, device="cuda")
+            seq.solver.solve(y0)  # warm-up (graph instantiation)
+            seq.time_calls = True
+            r0 = seq.run("nat")
+            t_seq = solve_ms(seq)
+            # the equal-iteration case uses the sample of median iteration count,
+            # so that its fixed per-call cost weighs as in a typical solve
+            j_med = int(np.argsort(r0["I"], kind="stable")[len(r0["I"]) // 2])
+            y_med = torch.from_numpy(r0["y"][j_med:j_med + 1].copy()).to("cuda")
+            seq.call_events = []
+            for _ in range(5):
+                seq._call(y_med)
+            t1 = float(np.median([ms for _, ms in seq.call_times()]))
+            del seq
+            res = {"points": len(r0["I"]), "levels": [b - a for a, b in r0["levels"]],
+                   "iters_min": int(r0["I"].min()), "iters_max": int(r0["I"].max()),
+                   "iters_mean": float(r0["I"].mean()), "sequential_solve_ms": t_seq,
+                   "sigma_sample_iters": int(r0["I"][j_med]), "sigma_one_solve_ms": t1, "S": {}}
+            for S in S_list:
+                ad = Adaptive(h, wl, S=S, precond=pc)
+                ad.run("nat")  # warm-up: instantiates every level's loop graph
+                Ms = min(512, ad.solver.Emax * S)
+                ys = y_med.expand(Ms, -1).contiguous()
+                ad.solver.solve(ys)
+                ad.time_calls = True
+                ad.call_events = []
+                ad._call(ys)
+                sigma = Ms * t1 / ad.call_times()[0][1]
+                row = {"sigma": sigma}
+                same_grid = True
+                for g in ("sur", "par", "nat"):
+                    r = ad.run(g)
+                    t = solve_ms(ad)
+                    same_grid &= bool(np.array_equal(r["lvl"], r0["lvl"]))
+                    R = ratios(r)
+                    row[g] = {"R_levels": R["run"][0], "R": R["run"][1], "speedup": t_seq / t,
+                              "pred_speedup": sigma / R["run"][1], "solve_ms": t}
+                    if g == "sur":
+                        row["its"] = {"R_levels": R["its"][0], "R": R["its"][1],
+                                      "pred_speedup": sigma / R["its"][1]}
+                        row["sur_pred_rel_err"] = [
+                            float(np.mean(np.abs(pr - r["I"][a:b])) / np.mean(r["I"][a:b]))
+                            for (a, b), pr in list(zip(r["levels"], r["preds"]))[1:]]
+                        row["max_iter_diff_vs_sequential"] = int(np.max(np.abs(r["I"] - r0["I"])))
+                row["same_grid_as_sequential"] = same_grid
+                res["S"][S] = row
+                del ad
+                torch.cuda.empty_cache()
+            out[name][pc] = res
     return out
 
 

@@ -172,6 +172,62 @@ int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   double rtol, int maxit, int32_t *iters, double *relres, int32_t *status,
                   void *work, size_t work_bytes, void *stream);
 
+/* ---- Multigrid-preconditioned ensemble CG (the trilinear problems) --------
+ * Section 4 preconditions CG with multigrid (a Chebyshev-smoothed hierarchy,
+ * coarsest level solved directly), instantiated on the ensemble scalar.  For
+ * ENS_Q1_3D_KL / ENS_Q1_3D_DISC with n = 2^k - 1 (k >= 2) interior nodes per
+ * axis this library builds the nested trilinear hierarchy per sample:
+ * levels n, (n-1)/2, ..., 3; P = trilinear interpolation; coarse operators
+ * P^T A P (Galerkin); a degree-2 Chebyshev smoother on D^-1 A over
+ * [lambda/30, lambda], lambda the sample's Gershgorin bound
+ * max_i sum_j |a_ij| / a_ii; a dense Cholesky solve on the 27-unknown coarsest
+ * level; one V-cycle (pre-smooth, coarse correction, post-smooth) per CG
+ * iteration.  Other kinds or sizes: ENS_ENOTSUP / ENS_EINVAL. */
+
+/* Bytes of caller workspace the three calls below need (0 when unsupported). */
+size_t ens_mg_workspace_size(const ens_problem *p, int S, int E);
+
+/* Build the hierarchy of E ensembles from the fine values vals[E][nnz][S]
+ * (device f64; rowptr/colidx the problem's graph from ens_pattern) into work:
+ * coarse graphs and Galerkin values, inverse diagonals, Gershgorin bounds and
+ * Chebyshev coefficients of every level, the coarsest level's factor.  A lane
+ * whose row ratios are not all finite and positive, or whose coarsest
+ * factorisation meets a non-positive pivot, is marked unusable (its solve
+ * reports ENS_LANE_BADINPUT).  The products, sums and roots of the setup are
+ * each rounded on their own, in the order of the definitions, so the coarse
+ * values match a plain host computation bit for bit.  No synchronisation. */
+int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+                 const int32_t *colidx, const double *vals, void *work, size_t work_bytes,
+                 void *stream);
+
+/* Copy level `level` of the hierarchy in `work` out (device, f64): its Galerkin
+ * values vals_out[E][nnz_l][S] (levels >= 1; level 0 is the caller's own) and
+ * the Gershgorin bounds lmax_out[E][S] (0 for an unusable lane).  Either may
+ * be NULL.  An inspection aid (no counterpart in the paper). */
+int ens_mg_level(ens_handle h, const ens_problem *p, int S, int E, int level, double *vals_out,
+                 double *lmax_out, const void *work, size_t work_bytes, void *stream);
+
+/* z[E][J][S] = one V-cycle applied to r[E][J][S] (device f64) with the
+ * hierarchy of the last ens_mg_setup on `work` (same vals).  Lanes marked
+ * unusable get undefined values.  No synchronisation. */
+int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+                 const int32_t *colidx, const double *vals, const double *r, double *z,
+                 void *work, size_t work_bytes, void *stream);
+
+/* CG preconditioned by one V-cycle per iteration, with the conventions and
+ * outputs of ens_pcg_solve (x = 0 start, per-sample inner products, the
+ * unpreconditioned ||r_s|| <= rtol ||b_s|| test after each update, frozen lanes,
+ * status codes; active may be NULL).  Needs ens_mg_setup on `work` with the
+ * same vals first.  The host launches the iterations and reads the live-lane
+ * count back every two to four of them (the call synchronises the stream);
+ * each lane still stops at its own iteration, so results do not depend on that
+ * cadence.  Deterministic: per-lane results depend only on the lane's data, S
+ * and J. */
+int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+                    const int32_t *colidx, const double *vals, const double *b, double *x,
+                    const uint8_t *active, double rtol, int maxit, int32_t *iters, double *relres,
+                    int32_t *status, void *work, size_t work_bytes, void *stream);
+
 /* Bytes of caller workspace ens_solve_stream needs (0 for bad arguments). */
 size_t ens_stream_workspace_size(const ens_problem *p, int S, int E);
 

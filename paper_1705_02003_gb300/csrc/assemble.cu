@@ -350,6 +350,23 @@ __device__ __forceinline__ double q13_a(const KLField &f, const double *y, doubl
     return 0.1 + ahat * exp(s);
 }
 
+// The 1-D mode values at the element centroids (m + 1/2) h, m = 0..n, are
+// the only trigonometry of the field: each block tabulates them once in
+// shared memory with the expressions of q13_a, so every element coefficient
+// is the same number as when evaluated directly.
+constexpr int kQ13MaxCells = 401;  // n + 1 for the largest n the problem check admits
+
+__device__ __forceinline__ double q13_a_tab(const KLField &f, const double *te, const double *to, const double *y,
+                                            double ahat, int ex, int ey, int ez)
+{
+    const double e0 = te[ex], o0 = to[ex], e1 = te[ey], o1 = to[ey], e2 = te[ez], o2 = to[ez];
+    double s = f.sl[0] * (e0 * e1 * e2) * y[0];
+    s += f.sl[1] * (o0 * e1 * e2) * y[1];
+    s += f.sl[2] * (e0 * o1 * e2) * y[2];
+    s += f.sl[3] * (e0 * e1 * o2) * y[3];
+    return 0.1 + ahat * exp(s);
+}
+
 template <typename V>
 __global__ void k_assemble_q13(int n, int kind, KLField f, int S, int E, const double *__restrict__ xi,
                                const int32_t *__restrict__ rowptr, V *__restrict__ vals, double *__restrict__ dinv,
@@ -358,6 +375,13 @@ __global__ void k_assemble_q13(int n, int kind, KLField f, int S, int E, const d
     const int n2 = n * n, J = n2 * n;
     const long long total = lanes ? (long long)nlanes * J : (long long)E * J * S;
     const double h = 1.0 / (double)(n + 1);
+    __shared__ double te[kQ13MaxCells], to[kQ13MaxCells];
+    for (int m = threadIdx.x; m <= n && m < kQ13MaxCells; m += blockDim.x) {
+        const double x = ((double)m + 0.5) * h;
+        te[m] = f.ie * cos(f.we * (x - 0.5));
+        to[m] = f.io * sin(f.wo * (x - 0.5));
+    }
+    __syncthreads();
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         int s, row, e;
@@ -381,7 +405,7 @@ __global__ void k_assemble_q13(int n, int kind, KLField f, int S, int E, const d
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const int ex = i + (q & 1), ey = j + ((q >> 1) & 1), ez = l + (q >> 2);
-            a[q] = q13_a(f, y, ahat, ((double)ex + 0.5) * h, ((double)ey + 0.5) * h, ((double)ez + 0.5) * h);
+            a[q] = q13_a_tab(f, te, to, y, ahat, ex, ey, ez);
         }
         const long long base = (long long)e * nnz * S + s;
         long long k = rowptr[row];

@@ -1,0 +1,888 @@
+// mg.cu -- ensemble multigrid V-cycle preconditioner and multigrid-preconditioned
+// CG for the trilinear problems (ENS_Q1_3D_KL / ENS_Q1_3D_DISC).
+//
+// Section 4 preconditions CG with a multigrid hierarchy whose levels are
+// smoothed by a second-order Chebyshev polynomial and whose coarsest level is
+// solved directly; like the rest of that solver it is instantiated on the
+// ensemble scalar, so every level stores S samples per nonzero and every
+// operation is per sample.  On the structured (n + 1)^3-cell mesh this
+// library uses the nested trilinear hierarchy (the mesh is structured, so the
+// aggregates of an algebraic method are known in advance):
+//   - levels n_0 = n, n_{l+1} = (n_l - 1) / 2 down to 3 (n = 2^k - 1, k >= 2);
+//     coarse node c sits on fine node 2c + 1;
+//   - P = trilinear interpolation (weights 1, 1/2 per axis), R = P^T;
+//   - coarse operators A_{l+1} = P^T A_l P (Galerkin), per sample;
+//   - smoother: the degree-2 Chebyshev semi-iteration on D^-1 A over
+//     [lambda_max / 30, lambda_max], lambda_max the per-sample Gershgorin bound
+//     max_i sum_j |a_ij| / a_ii;
+//   - coarsest level (27 unknowns): per-sample dense Cholesky, applied as the
+//     explicit inverse built from it;
+//   - one V-cycle per CG iteration (pre-smooth from 0, restrict, recurse,
+//     prolong-add, post-smooth).
+// The setup (Galerkin products, Gershgorin bounds, Cholesky) rounds every
+// product and sum on its own in the order of the textbook triple sum, so it
+// reproduces a plain host computation bit for bit; the V-cycle itself uses
+// fused multiply-adds.
+//
+// Layout: every vector of level l is [E][J_l][S] f64, every matrix
+// [E][nnz_l][S] f64 (level 0 is the caller's), the coarsest operator's
+// inverse [E][729][S].  Per-sample scalars are [E][S].
+#include "ens_common.cuh"
+
+#include <cmath>
+
+namespace ens {
+namespace {
+
+constexpr int kMgMaxLev = 8;
+constexpr int kRedRows = 256;   // rows per block of the CG reduction kernels
+constexpr double kRatio = 30.0;
+constexpr int kCoarseJ = 27;
+constexpr int kInv = kCoarseJ * kCoarseJ;
+
+struct MgLevel {
+    int n = 0, J = 0;
+    int64_t nnz = 0;
+    int32_t *rp = nullptr, *ci = nullptr;  // coarse levels' graph
+    double *vals = nullptr;                // coarse levels' values
+    double *dinv = nullptr;
+    double *coef = nullptr;                // [E][S][4]: 1/theta, c1, c2, -
+    unsigned long long *lmax = nullptr;    // [E][S] bits of the Gershgorin bound
+    double *rhs = nullptr, *e = nullptr, *t = nullptr, *d = nullptr, *res = nullptr;
+};
+
+struct MgWork {
+    int L = 0;
+    MgLevel lv[kMgMaxLev];
+    double *cinv = nullptr;  // [E][27 * 27][S]: inverse of the coarsest operator
+    int *bad = nullptr;      // [E][S]
+    // CG state
+    double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
+    double *part0 = nullptr, *part1 = nullptr;  // [E][nblk][S]
+    double *rz = nullptr, *rr = nullptr, *alpha = nullptr, *beta = nullptr, *bnorm = nullptr;
+    int *k = nullptr, *live = nullptr, *ens_live = nullptr, *live_total = nullptr;
+    int nblk = 0;
+    size_t bytes = 0;
+};
+
+bool mg_levels(int n, int *ns, int *L)
+{
+    if (n < 3) return false;
+    for (int m = n + 1; m > 1; m >>= 1)
+        if (m & 1) return false;
+    int k = 0;
+    ns[k++] = n;
+    while (ns[k - 1] > 3) {
+        if (k >= kMgMaxLev) return false;
+        ns[k] = (ns[k - 1] - 1) / 2;
+        k++;
+    }
+    *L = k;
+    return true;
+}
+
+// Lay the workspace out from `base` (nullptr: only count the bytes).
+bool mg_layout(const ens_problem *p, int S, int E, char *base, MgWork *w)
+{
+    int ns[kMgMaxLev], L;
+    if (!mg_levels(p->n, ns, &L)) return false;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *ptr = base ? base + off : nullptr;
+        off += align256(bytes);
+        return ptr;
+    };
+    const size_t ES = (size_t)E * S;
+    w->L = L;
+    for (int l = 0; l < L; l++) {
+        MgLevel &v = w->lv[l];
+        v.n = ns[l];
+        v.J = ns[l] * ns[l] * ns[l];
+        v.nnz = (int64_t)(3 * ns[l] - 2) * (3 * ns[l] - 2) * (3 * ns[l] - 2);
+        const size_t vec = ES * v.J * sizeof(double);
+        if (l > 0) {
+            v.rp = (int32_t *)take(sizeof(int32_t) * (v.J + 1));
+            v.ci = (int32_t *)take(sizeof(int32_t) * v.nnz);
+            v.vals = (double *)take(ES * v.nnz * sizeof(double));
+            v.rhs = (double *)take(vec);
+        }
+        v.dinv = (double *)take(vec);
+        v.coef = (double *)take(ES * 4 * sizeof(double));
+        v.lmax = (unsigned long long *)take(ES * sizeof(unsigned long long));
+        v.e = (double *)take(vec);
+        if (l < L - 1) {
+            v.t = (double *)take(vec);
+            v.d = (double *)take(vec);
+            v.res = (double *)take(vec);
+        }
+    }
+    w->cinv = (double *)take(ES * kInv * sizeof(double));
+    w->bad = (int *)take(ES * sizeof(int));
+    const int J = w->lv[0].J;
+    const size_t vec0 = ES * J * sizeof(double);
+    w->r = (double *)take(vec0);
+    w->p = (double *)take(vec0);
+    w->q = (double *)take(vec0);
+    w->z = w->lv[0].e;
+    w->nblk = (J + kRedRows - 1) / kRedRows;
+    w->part0 = (double *)take(ES * w->nblk * sizeof(double));
+    w->part1 = (double *)take(ES * w->nblk * sizeof(double));
+    w->rz = (double *)take(ES * sizeof(double));
+    w->rr = (double *)take(ES * sizeof(double));
+    w->alpha = (double *)take(ES * sizeof(double));
+    w->beta = (double *)take(ES * sizeof(double));
+    w->bnorm = (double *)take(ES * sizeof(double));
+    w->k = (int *)take(ES * sizeof(int));
+    w->live = (int *)take(ES * sizeof(int));
+    w->ens_live = (int *)take((size_t)E * sizeof(int));
+    w->live_total = (int *)take(sizeof(int));
+    w->bytes = off;
+    return true;
+}
+
+// ---- setup kernels (one row-lane per thread: lane t % S, row blockIdx.x G + t / S) ----
+
+__device__ __forceinline__ void row_lane(int S, int *s, int *i)
+{
+    const int G = blockDim.x / S;
+    *s = threadIdx.x % S;
+    *i = blockIdx.x * G + threadIdx.x / S;
+}
+
+// D^-1 and the Gershgorin ratio sum_j |a_ij| / a_ii of every row-lane; the
+// per-lane maximum by an atomic maximum on the bits (positive doubles order
+// like their bit patterns); a ratio that is not finite and positive marks the
+// lane unusable.
+__global__ void k_mg_diag(int J, int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ vals, double *__restrict__ dinv,
+                          unsigned long long *__restrict__ lmax, int *__restrict__ bad)
+{
+    int s, i;
+    row_lane(S, &s, &i);
+    const int e = blockIdx.y;
+    if (i >= J) return;
+    const int64_t nnz = rp[J];
+    const double *v = vals + (size_t)e * nnz * S + s;
+    double sum = 0.0, d = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+        const double a = v[(size_t)k * S];
+        sum = dadd(sum, fabs(a));
+        if (ci[k] == i) d = a;
+    }
+    const double ratio = __ddiv_rn(sum, d);
+    dinv[((size_t)e * J + i) * S + s] = __ddiv_rn(1.0, d);
+    if (!(ratio > 0.0) || !isfinite(ratio))
+        bad[e * S + s] = 1;
+    else
+        atomicMax(lmax + e * S + s, (unsigned long long)__double_as_longlong(ratio));
+}
+
+// Chebyshev coefficients of each lane from its bound: 1/theta, and c1, c2 of the second step.
+__global__ void k_mg_coef(int ES, const unsigned long long *__restrict__ lmax, double *__restrict__ coef)
+{
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= ES) return;
+    const double lm = __longlong_as_double((long long)lmax[L]);
+    const double lmin = lm / kRatio;
+    const double theta = (lm + lmin) / 2.0, delta = (lm - lmin) / 2.0;
+    const double sigma = theta / delta;
+    const double rho0 = 1.0 / sigma;
+    const double rho1 = 1.0 / (2.0 * sigma - rho0);
+    coef[4 * L + 0] = 1.0 / theta;
+    coef[4 * L + 1] = rho1 * rho0;
+    coef[4 * L + 2] = 2.0 * rho1 / delta;
+    coef[4 * L + 3] = 0.0;
+}
+
+// Per-axis coarse parents of fine coordinate f: (index, weight), ascending.
+__device__ __forceinline__ int parents(int f, int nc, int *c, double *w)
+{
+    int m = 0;
+    if (f & 1) {
+        c[0] = (f - 1) >> 1;
+        w[0] = 1.0;
+        m = 1;
+    } else {
+        const int a = (f >> 1) - 1, b = f >> 1;
+        if (a >= 0) { c[m] = a; w[m] = 0.5; m++; }
+        if (b < nc) { c[m] = b; w[m] = 0.5; m++; }
+    }
+    return m;
+}
+
+__device__ __forceinline__ double w1(int f, int c)
+{
+    const int d = f - (2 * c + 1);
+    return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0);
+}
+
+// A_c = P^T A_f P for every coarse row-lane, one coarse entry (I, J) at a
+// time: its contributions w_i w_j a_ij are added in the order of the triple
+// sum (fine nodes i of I ascending, then the columns j of row i ascending,
+// restricted to the children of J), each product and sum rounded on its own;
+// the weights are powers of two, so the products are exact.  Row i's columns
+// are its 3x3x3 neighbourhood clipped to the grid, in lexicographic order, so
+// the position of column j in the row follows from the clipped box.
+__global__ void k_mg_galerkin(int nf, int nc, int S, const int32_t *__restrict__ rpf, const double *__restrict__ vf,
+                              const int32_t *__restrict__ rpc, const int32_t *__restrict__ cic,
+                              double *__restrict__ vc)
+{
+    int s, I;
+    row_lane(S, &s, &I);
+    const int e = blockIdx.y;
+    const int Jc = nc * nc * nc, Jf = nf * nf * nf;
+    if (I >= Jc) return;
+    const int I0 = I % nc, I1 = (I / nc) % nc, I2 = I / (nc * nc);
+    const int64_t nnzf = rpf[Jf], nnzc = rpc[Jc];
+    const double *v = vf + (size_t)e * nnzf * S + s;
+    double *out = vc + (size_t)e * nnzc * S + s;
+    for (int kc = rpc[I]; kc < rpc[I + 1]; kc++) {
+        const int Jn = cic[kc];
+        const int J0 = Jn % nc, J1 = (Jn / nc) % nc, J2 = Jn / (nc * nc);
+        double acc = 0.0;
+        for (int i2 = 2 * I2; i2 <= 2 * I2 + 2; i2++)
+            for (int i1 = 2 * I1; i1 <= 2 * I1 + 2; i1++)
+                for (int i0 = 2 * I0; i0 <= 2 * I0 + 2; i0++) {
+                    // row box of i and the children box of J, per axis
+                    const int rb0 = max(i0 - 1, 0), rb1 = max(i1 - 1, 0), rb2 = max(i2 - 1, 0);
+                    const int rn0 = min(i0 + 1, nf - 1) - rb0 + 1, rn1 = min(i1 + 1, nf - 1) - rb1 + 1;
+                    const int lo0 = max(rb0, 2 * J0), hi0 = min(i0 + 1, min(nf - 1, 2 * J0 + 2));
+                    const int lo1 = max(rb1, 2 * J1), hi1 = min(i1 + 1, min(nf - 1, 2 * J1 + 2));
+                    const int lo2 = max(rb2, 2 * J2), hi2 = min(i2 + 1, min(nf - 1, 2 * J2 + 2));
+                    if (lo0 > hi0 || lo1 > hi1 || lo2 > hi2) continue;
+                    const int i = i0 + nf * (i1 + nf * i2);
+                    const double wi = dmul(dmul(w1(i0, I0), w1(i1, I1)), w1(i2, I2));
+                    const int base = rpf[i];
+                    for (int j2 = lo2; j2 <= hi2; j2++)
+                        for (int j1 = lo1; j1 <= hi1; j1++)
+                            for (int j0 = lo0; j0 <= hi0; j0++) {
+                                const int k = base + ((j2 - rb2) * rn1 + (j1 - rb1)) * rn0 + (j0 - rb0);
+                                const double wj = dmul(dmul(w1(j0, J0), w1(j1, J1)), w1(j2, J2));
+                                acc = dadd(acc, dmul(dmul(wi, wj), v[(size_t)k * S]));
+                            }
+                }
+        out[(size_t)kc * S] = acc;
+    }
+}
+
+// The coarsest level (27 unknowns), one block per lane: Cholesky A = L L^T in
+// shared memory by one thread in the textbook order (each product, difference,
+// quotient and root rounded on its own), then thread j < 27 solves
+// L L^T x = e_j for column j of A^-1.  The V-cycle's coarsest solve is then a
+// 27 x 27 product.
+__global__ void k_mg_chol(int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ vals, double *__restrict__ cinv, int *__restrict__ bad)
+{
+    __shared__ double A[kInv];
+    __shared__ double Lf[kInv];
+    __shared__ int fail;
+    const int s = blockIdx.x, e = blockIdx.y;
+    const int64_t nnz = rp[kCoarseJ];
+    for (int q = threadIdx.x; q < kInv; q += blockDim.x) {
+        A[q] = 0.0;
+        Lf[q] = 0.0;
+    }
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kCoarseJ; i += blockDim.x)
+        for (int k = rp[i]; k < rp[i + 1]; k++) A[i * kCoarseJ + ci[k]] = vals[((size_t)e * nnz + k) * S + s];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < kCoarseJ && !fail; j++) {
+            double sj = A[j * kCoarseJ + j];
+            for (int k = 0; k < j; k++) sj = dsub(sj, dmul(Lf[j * kCoarseJ + k], Lf[j * kCoarseJ + k]));
+            if (!(sj > 0.0)) {
+                fail = 1;
+                break;
+            }
+            const double d = __dsqrt_rn(sj);
+            Lf[j * kCoarseJ + j] = d;
+            for (int i = j + 1; i < kCoarseJ; i++) {
+                double t = A[i * kCoarseJ + j];
+                for (int k = 0; k < j; k++) t = dsub(t, dmul(Lf[i * kCoarseJ + k], Lf[j * kCoarseJ + k]));
+                Lf[i * kCoarseJ + j] = __ddiv_rn(t, d);
+            }
+        }
+        if (fail) bad[e * S + s] = 1;
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j < kCoarseJ) {
+        double y[kCoarseJ];
+#pragma unroll 1
+        for (int i = 0; i < kCoarseJ; i++) {
+            double acc = i == j ? 1.0 : 0.0;
+#pragma unroll 1
+            for (int k = 0; k < i; k++) acc = fma(-Lf[i * kCoarseJ + k], y[k], acc);
+            y[i] = acc / Lf[i * kCoarseJ + i];
+        }
+#pragma unroll 1
+        for (int i = kCoarseJ - 1; i >= 0; i--) {
+            double acc = y[i];
+#pragma unroll 1
+            for (int k = i + 1; k < kCoarseJ; k++) acc = fma(-Lf[k * kCoarseJ + i], y[k], acc);
+            y[i] = acc / Lf[i * kCoarseJ + i];
+        }
+#pragma unroll 1
+        for (int i = 0; i < kCoarseJ; i++) cinv[((size_t)e * kInv + i * kCoarseJ + j) * S + s] = y[i];
+    }
+}
+
+// ---- V-cycle kernels ----------------------------------------------------------
+
+__device__ __forceinline__ bool ens_skip(const int *ens_live, int e) { return ens_live && ens_live[e] == 0; }
+
+// One row-lane of A x, nonzeros in order.  (Reading the row in chunks of nine,
+// all loads of a chunk issued before its multiply-adds, took 80 registers and
+// three resident blocks per SM instead of eight and made the 31^3 solve 1.6-2x
+// slower, measured: here more warps hide the latency better than more loads
+// in flight per thread.)
+__device__ __forceinline__ double row_dot(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                          const double *__restrict__ v, const double *__restrict__ x, int i,
+                                          int S)
+{
+    double acc = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) acc = fma(v[(size_t)k * S], x[(size_t)ci[k] * S], acc);
+    return acc;
+}
+
+// First Chebyshev step: d = D^-1 (b - A x) / theta, x_out = x + d (x = 0 when x_in is null).
+__global__ void k_mg_cheb1(int J, int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ vals, const double *__restrict__ dinv,
+                           const double *__restrict__ coef, const double *__restrict__ b,
+                           const double *__restrict__ x_in, double *__restrict__ d, double *__restrict__ x_out,
+                           const int *__restrict__ ens_live)
+{
+    int s, i;
+    row_lane(S, &s, &i);
+    const int e = blockIdx.y;
+    if (i >= J || ens_skip(ens_live, e)) return;
+    const int64_t nnz = rp[J];
+    const size_t vb = (size_t)e * J * S + s, o = vb + (size_t)i * S;
+    double x0 = 0.0, res = b[o];
+    if (x_in) {
+        res -= row_dot(rp, ci, vals + (size_t)e * nnz * S + s, x_in + vb, i, S);
+        x0 = x_in[o];
+    }
+    const double dd = dinv[o] * res * coef[4 * (e * S + s)];
+    d[o] = dd;
+    x_out[o] = x0 + dd;
+}
+
+// Second Chebyshev step: d = c1 d + c2 D^-1 (b - A x), x_out = x + d.
+__global__ void k_mg_cheb2(int J, int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ vals, const double *__restrict__ dinv,
+                           const double *__restrict__ coef, const double *__restrict__ b,
+                           const double *__restrict__ x_in, double *__restrict__ d, double *__restrict__ x_out,
+                           const int *__restrict__ ens_live)
+{
+    int s, i;
+    row_lane(S, &s, &i);
+    const int e = blockIdx.y;
+    if (i >= J || ens_skip(ens_live, e)) return;
+    const int64_t nnz = rp[J];
+    const size_t vb = (size_t)e * J * S + s, o = vb + (size_t)i * S;
+    const double res = b[o] - row_dot(rp, ci, vals + (size_t)e * nnz * S + s, x_in + vb, i, S);
+    const double *c = coef + 4 * (e * S + s);
+    const double dd = fma(c[1], d[o], c[2] * (dinv[o] * res));
+    d[o] = dd;
+    x_out[o] = x_in[o] + dd;
+}
+
+// res = b - A x
+__global__ void k_mg_resid(int J, int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ vals, const double *__restrict__ b,
+                           const double *__restrict__ x, double *__restrict__ res, const int *__restrict__ ens_live)
+{
+    int s, i;
+    row_lane(S, &s, &i);
+    const int e = blockIdx.y;
+    if (i >= J || ens_skip(ens_live, e)) return;
+    const int64_t nnz = rp[J];
+    const size_t vb = (size_t)e * J * S + s, o = vb + (size_t)i * S;
+    res[o] = b[o] - row_dot(rp, ci, vals + (size_t)e * nnz * S + s, x + vb, i, S);
+}
+
+// rc = P^T rf: the 27 fine nodes of each coarse node, ascending.
+__global__ void k_mg_restrict(int nf, int nc, int S, const double *__restrict__ rf, double *__restrict__ rc,
+                              const int *__restrict__ ens_live)
+{
+    int s, I;
+    row_lane(S, &s, &I);
+    const int e = blockIdx.y;
+    const int Jc = nc * nc * nc, Jf = nf * nf * nf;
+    if (I >= Jc || ens_skip(ens_live, e)) return;
+    const int I0 = I % nc, I1 = (I / nc) % nc, I2 = I / (nc * nc);
+    const double *r = rf + (size_t)e * Jf * S + s;
+    double acc = 0.0;
+    for (int i2 = 2 * I2; i2 <= 2 * I2 + 2; i2++)
+        for (int i1 = 2 * I1; i1 <= 2 * I1 + 2; i1++)
+            for (int i0 = 2 * I0; i0 <= 2 * I0 + 2; i0++) {
+                const double w = w1(i0, I0) * w1(i1, I1) * w1(i2, I2);
+                acc = fma(w, r[(size_t)(i0 + nf * (i1 + nf * i2)) * S], acc);
+            }
+    rc[((size_t)e * Jc + I) * S + s] = acc;
+}
+
+// ef += P ec: the (up to 8) coarse parents of each fine node, ascending.
+__global__ void k_mg_prolong_add(int nf, int nc, int S, const double *__restrict__ ec, double *__restrict__ ef,
+                                 const int *__restrict__ ens_live)
+{
+    int s, i;
+    row_lane(S, &s, &i);
+    const int e = blockIdx.y;
+    const int Jc = nc * nc * nc, Jf = nf * nf * nf;
+    if (i >= Jf || ens_skip(ens_live, e)) return;
+    const int f0 = i % nf, f1 = (i / nf) % nf, f2 = i / (nf * nf);
+    int c0[2], c1[2], c2[2];
+    double u0[2], u1[2], u2[2];
+    const int m0 = parents(f0, nc, c0, u0), m1 = parents(f1, nc, c1, u1), m2 = parents(f2, nc, c2, u2);
+    const double *c = ec + (size_t)e * Jc * S + s;
+    double acc = 0.0;
+    for (int b2 = 0; b2 < m2; b2++)
+        for (int b1 = 0; b1 < m1; b1++)
+            for (int b0 = 0; b0 < m0; b0++)
+                acc = fma(u0[b0] * u1[b1] * u2[b2], c[(size_t)(c0[b0] + nc * (c1[b1] + nc * c2[b2])) * S], acc);
+    const size_t o = ((size_t)e * Jf + i) * S + s;
+    ef[o] = ef[o] + acc;
+}
+
+// Coarsest level: e = A^-1 r, one row-lane per thread (27 products, ascending).
+__global__ void k_mg_coarse_solve(int S, const double *__restrict__ cinv, const double *__restrict__ r,
+                                  double *__restrict__ x, const int *__restrict__ ens_live)
+{
+    int s, i;
+    row_lane(S, &s, &i);
+    const int e = blockIdx.y;
+    if (i >= kCoarseJ || ens_skip(ens_live, e)) return;
+    const double *a = cinv + ((size_t)e * kInv + i * kCoarseJ) * S + s;
+    const double *rv = r + (size_t)e * kCoarseJ * S + s;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < kCoarseJ; j++) acc = fma(a[(size_t)j * S], rv[(size_t)j * S], acc);
+    x[((size_t)e * kCoarseJ + i) * S + s] = acc;
+}
+
+// ---- CG kernels: 256-row blocks, per-lane block partial sums ---------------------
+
+// Per-lane sum over the block's row groups, pairwise in a fixed order; the
+// result is valid in threads t < S.
+__device__ __forceinline__ double block_lane_sum(double v, int S, double *sh)
+{
+    const int t = threadIdx.x, G = blockDim.x / S;
+    sh[t] = v;
+    __syncthreads();
+    for (int st = G / 2; st > 0; st >>= 1) {
+        if (t / S < st) sh[t] = dadd(sh[t], sh[t + st * S]);
+        __syncthreads();
+    }
+    return sh[t];
+}
+
+struct CgArgs {
+    int J, S, E, nblk, maxit;
+    double rtol;
+    const uint8_t *active;
+    int32_t *iters, *status;
+    double *relres;
+};
+
+// x = 0, r = b; block partials of b^T b (part0).
+__global__ void k_mgcg_init(int J, int S, int nblk, const double *__restrict__ b, double *__restrict__ x,
+                            double *__restrict__ r, double *__restrict__ part)
+{
+    __shared__ double sh[kBlock];
+    const int e = blockIdx.y, s = threadIdx.x % S, G = blockDim.x / S;
+    const int r0 = blockIdx.x * kRedRows, r1 = min(J, r0 + kRedRows);
+    double acc = 0.0;
+    for (int i = r0 + threadIdx.x / S; i < r1; i += G) {
+        const size_t o = ((size_t)e * J + i) * S + s;
+        const double bv = b[o];
+        x[o] = 0.0;
+        r[o] = bv;
+        acc = fma(bv, bv, acc);
+    }
+    const double tot = block_lane_sum(acc, S, sh);
+    if (threadIdx.x < S) part[((size_t)e * nblk + blockIdx.x) * S + s] = tot;
+}
+
+// Block partials of u^T v for live lanes (all lanes when live is null).
+__global__ void k_mgcg_dot(int J, int S, int nblk, const double *__restrict__ u, const double *__restrict__ v,
+                           const int *__restrict__ live, const int *__restrict__ ens_live, double *__restrict__ part)
+{
+    __shared__ double sh[kBlock];
+    const int e = blockIdx.y, s = threadIdx.x % S, G = blockDim.x / S;
+    if (ens_skip(ens_live, e)) return;
+    const bool on = !live || live[e * S + s];
+    const int r0 = blockIdx.x * kRedRows, r1 = min(J, r0 + kRedRows);
+    double acc = 0.0;
+    if (on)
+        for (int i = r0 + threadIdx.x / S; i < r1; i += G) {
+            const size_t o = ((size_t)e * J + i) * S + s;
+            acc = fma(u[o], v[o], acc);
+        }
+    const double tot = block_lane_sum(acc, S, sh);
+    if (threadIdx.x < S) part[((size_t)e * nblk + blockIdx.x) * S + s] = tot;
+}
+
+// q = A p for live lanes, one row-lane per thread (p^T q follows in k_mgcg_dot).
+__global__ void k_mgcg_spmv(int J, int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ vals, const double *__restrict__ p, double *__restrict__ q,
+                            const int *__restrict__ live, const int *__restrict__ ens_live)
+{
+    int s, i;
+    row_lane(S, &s, &i);
+    const int e = blockIdx.y;
+    if (i >= J || ens_skip(ens_live, e) || !live[e * S + s]) return;
+    const int64_t nnz = rp[J];
+    const size_t vb = (size_t)e * J * S + s;
+    q[vb + (size_t)i * S] = row_dot(rp, ci, vals + (size_t)e * nnz * S + s, p + vb, i, S);
+}
+
+// x += alpha p, r -= alpha q and block partials of r^T r for live lanes.
+__global__ void k_mgcg_update(int J, int S, int nblk, double *__restrict__ x, double *__restrict__ r,
+                              const double *__restrict__ p, const double *__restrict__ q,
+                              const double *__restrict__ alpha, const int *__restrict__ live,
+                              const int *__restrict__ ens_live, double *__restrict__ part)
+{
+    __shared__ double sh[kBlock];
+    const int e = blockIdx.y, s = threadIdx.x % S, G = blockDim.x / S;
+    if (ens_skip(ens_live, e)) return;
+    const int L = e * S + s;
+    const bool on = live[L] != 0;
+    const double al = on ? alpha[L] : 0.0;
+    const int r0 = blockIdx.x * kRedRows, r1 = min(J, r0 + kRedRows);
+    double acc = 0.0;
+    if (on)
+        for (int i = r0 + threadIdx.x / S; i < r1; i += G) {
+            const size_t o = ((size_t)e * J + i) * S + s;
+            x[o] = fma(al, p[o], x[o]);
+            const double rv = fma(-al, q[o], r[o]);
+            r[o] = rv;
+            acc = fma(rv, rv, acc);
+        }
+    const double tot = block_lane_sum(acc, S, sh);
+    if (threadIdx.x < S) part[((size_t)e * nblk + blockIdx.x) * S + s] = tot;
+}
+
+// p = z + beta p for live lanes; p = z for every lane when beta is null.
+__global__ void k_mgcg_dir(int J, int S, const double *__restrict__ z, double *__restrict__ p,
+                           const double *__restrict__ beta, const int *__restrict__ live,
+                           const int *__restrict__ ens_live)
+{
+    int s, i;
+    row_lane(S, &s, &i);
+    const int e = blockIdx.y;
+    if (i >= J || ens_skip(ens_live, e)) return;
+    const int L = e * S + s;
+    const size_t o = ((size_t)e * J + i) * S + s;
+    if (!beta)
+        p[o] = z[o];
+    else if (live[L])
+        p[o] = fma(beta[L], p[o], z[o]);
+}
+
+// The lane totals of nblk block partials: thread group g sums partials
+// g, g + G, ... in turn, then the groups combine pairwise (fixed order).
+__device__ double lane_total(const double *__restrict__ part, int nblk, int S, int e, double *sh)
+{
+    const int t = threadIdx.x, s = t % S, g = t / S, G = blockDim.x / S;
+    double v = 0.0;
+    for (int b = g; b < nblk; b += G) v = dadd(v, part[((size_t)e * nblk + b) * S + s]);
+    return block_lane_sum(v, S, sh);
+}
+
+__device__ __forceinline__ void mg_freeze(const CgArgs &a, int *live, int L, int st, int it, double relres,
+                                          int *dead)
+{
+    live[L] = 0;
+    a.status[L] = st;
+    a.iters[L] = it;
+    a.relres[L] = relres;
+    atomicAdd(dead, 1);
+}
+
+// Kinds of the per-lane finishing step.
+enum { FIN_INIT = 0, FIN_ALPHA = 1, FIN_CONV = 2, FIN_BETA = 3 };
+
+__global__ void k_mgcg_final(CgArgs a, int kind, const double *__restrict__ part0, const double *__restrict__ part1,
+                             MgWork w)
+{
+    __shared__ double sh[kBlock];
+    __shared__ int dead, born;
+    const int e = blockIdx.x, S = a.S;
+    if (kind != FIN_INIT && w.ens_live[e] == 0) return;
+    if (threadIdx.x == 0) dead = born = 0;
+    const double t0 = lane_total(part0, a.nblk, S, e, sh);
+    __syncthreads();
+    double t1 = 0.0;
+    if (kind == FIN_INIT) t1 = lane_total(part1, a.nblk, S, e, sh);
+    if (threadIdx.x < S) {
+        const int L = e * S + threadIdx.x;
+        if (kind == FIN_INIT) {
+            const double bsq = t0, rz = t1;
+            const int act = a.active ? (int)a.active[L] : 1;
+            int lv = 0;
+            w.k[L] = 0;
+            if (!act) {
+                a.status[L] = ENS_LANE_INACTIVE; a.iters[L] = 0; a.relres[L] = 0.0;
+            } else if (w.bad[L] || !isfinite(bsq) || !isfinite(rz)) {
+                a.status[L] = ENS_LANE_BADINPUT; a.iters[L] = 0;
+                a.relres[L] = __longlong_as_double(0x7ff8000000000000LL);
+            } else if (bsq == 0.0) {
+                a.status[L] = ENS_LANE_CONVERGED; a.iters[L] = 0; a.relres[L] = 0.0;
+            } else if (a.maxit <= 0) {
+                a.status[L] = ENS_LANE_MAXIT; a.iters[L] = 0; a.relres[L] = 1.0;
+            } else {
+                lv = 1;
+                w.bnorm[L] = sqrt(bsq);
+                w.rz[L] = rz;
+                w.rr[L] = bsq;
+                a.status[L] = ENS_LANE_MAXIT; a.iters[L] = 0; a.relres[L] = 1.0;
+            }
+            w.live[L] = lv;
+            if (lv) atomicAdd(&born, 1);
+        } else if (w.live[L]) {
+            if (kind == FIN_ALPHA) {
+                const double pq = t0;
+                if (!(pq > 0.0) || !isfinite(pq))
+                    mg_freeze(a, w.live, L, ENS_LANE_BREAKDOWN, w.k[L], sqrt(w.rr[L]) / w.bnorm[L], &dead);
+                else
+                    w.alpha[L] = w.rz[L] / pq;
+            } else if (kind == FIN_CONV) {
+                const int k = w.k[L] + 1;
+                w.k[L] = k;
+                w.rr[L] = t0;
+                const double res = sqrt(t0), bn = w.bnorm[L];
+                if (res <= a.rtol * bn)
+                    mg_freeze(a, w.live, L, ENS_LANE_CONVERGED, k, res / bn, &dead);
+                else if (k >= a.maxit)
+                    mg_freeze(a, w.live, L, ENS_LANE_MAXIT, k, res / bn, &dead);
+            } else {
+                const double rzn = t0;
+                w.beta[L] = rzn / w.rz[L];
+                w.rz[L] = rzn;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (kind == FIN_INIT) {
+            w.ens_live[e] = born;
+            if (born) atomicAdd(w.live_total, born);
+        } else if (dead) {
+            w.ens_live[e] -= dead;
+            atomicSub(w.live_total, dead);
+        }
+    }
+}
+
+// ---- host side ------------------------------------------------------------------
+
+inline dim3 rl_grid(int J, int S, int E) { return dim3((unsigned)((J + kBlock / S - 1) / (kBlock / S)), (unsigned)E); }
+
+int mg_check(ens_ctx *h, const char *who, const ens_problem *p, int S, int E, const void *work, size_t work_bytes,
+             MgWork *w)
+{
+    if (!h) return ENS_EINVAL;
+    if (!p) return set_error(h, ENS_EINVAL, std::string(who) + ": null problem");
+    if (p->kind != ENS_Q1_3D_KL && p->kind != ENS_Q1_3D_DISC)
+        return set_error(h, ENS_ENOTSUP, std::string(who) + ": the multigrid hierarchy is built for the trilinear problems only");
+    int J;
+    int64_t nnz;
+    std::string why;
+    if (problem_check(p, &J, &nnz, &why)) return set_error(h, ENS_EINVAL, std::string(who) + ": " + why);
+    if (!lane_count_ok(S) || E < 0) return set_error(h, ENS_EINVAL, std::string(who) + ": bad S / E");
+    if (!mg_layout(p, S, E, nullptr, w))
+        return set_error(h, ENS_EINVAL, std::string(who) + ": n must be 2^k - 1 (k >= 2)");
+    if (E > 0 && (!work || work_bytes < w->bytes)) return set_error(h, ENS_EINVAL, std::string(who) + ": workspace too small");
+    mg_layout(p, S, E, (char *)work, w);
+    return ENS_OK;
+}
+
+int mg_vcycle(ens_ctx *h, const MgWork &w, const int32_t *rp0, const int32_t *ci0, const double *vals0, int S,
+              int E, const double *rhs0, double *e0, const int *ens_live, cudaStream_t st)
+{
+    const int L = w.L;
+    auto graph = [&](int l, const int32_t **rp, const int32_t **ci, const double **v) {
+        *rp = l ? w.lv[l].rp : rp0;
+        *ci = l ? w.lv[l].ci : ci0;
+        *v = l ? w.lv[l].vals : vals0;
+    };
+    for (int l = 0; l < L - 1; l++) {
+        const MgLevel &v = w.lv[l];
+        const int32_t *rp, *ci;
+        const double *vals;
+        graph(l, &rp, &ci, &vals);
+        const double *rhs = l ? v.rhs : rhs0;
+        double *e = l ? v.e : e0;
+        const dim3 g = rl_grid(v.J, S, E);
+        k_mg_cheb1<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, v.dinv, v.coef, rhs, nullptr, v.d, v.t, ens_live);
+        k_mg_cheb2<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, v.dinv, v.coef, rhs, v.t, v.d, e, ens_live);
+        k_mg_resid<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, rhs, e, v.res, ens_live);
+        k_mg_restrict<<<rl_grid(w.lv[l + 1].J, S, E), kBlock, 0, st>>>(v.n, w.lv[l + 1].n, S, v.res, w.lv[l + 1].rhs,
+                                                                      ens_live);
+    }
+    {
+        const MgLevel &v = w.lv[L - 1];
+        const double *rhs = L > 1 ? v.rhs : rhs0;
+        double *e = L > 1 ? v.e : e0;
+        k_mg_coarse_solve<<<rl_grid(kCoarseJ, S, E), kBlock, 0, st>>>(S, w.cinv, rhs, e, ens_live);
+    }
+    for (int l = L - 2; l >= 0; l--) {
+        const MgLevel &v = w.lv[l];
+        const int32_t *rp, *ci;
+        const double *vals;
+        graph(l, &rp, &ci, &vals);
+        const double *rhs = l ? v.rhs : rhs0;
+        double *e = l ? v.e : e0;
+        const double *ec = w.lv[l + 1].e;  // l + 1 >= 1: a coarse level's correction
+        const dim3 g = rl_grid(v.J, S, E);
+        k_mg_prolong_add<<<g, kBlock, 0, st>>>(v.n, w.lv[l + 1].n, S, ec, e, ens_live);
+        k_mg_cheb1<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, v.dinv, v.coef, rhs, e, v.d, v.t, ens_live);
+        k_mg_cheb2<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, v.dinv, v.coef, rhs, v.t, v.d, e, ens_live);
+    }
+    ENS_LAUNCH_CHECK(h, "multigrid V-cycle");
+    return ENS_OK;
+}
+
+}  // namespace
+}  // namespace ens
+
+using namespace ens;
+
+extern "C" size_t ens_mg_workspace_size(const ens_problem *p, int S, int E)
+{
+    if (!p || (p->kind != ENS_Q1_3D_KL && p->kind != ENS_Q1_3D_DISC) || !lane_count_ok(S) || E < 0) return 0;
+    int J;
+    int64_t nnz;
+    std::string why;
+    if (problem_check(p, &J, &nnz, &why)) return 0;
+    MgWork w;
+    if (!mg_layout(p, S, E, nullptr, &w)) return 0;
+    return w.bytes;
+}
+
+extern "C" int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+                            const int32_t *colidx, const double *vals, void *work, size_t work_bytes, void *stream)
+{
+    MgWork w;
+    int rc = mg_check(h, "ens_mg_setup", p, S, E, work, work_bytes, &w);
+    if (rc) return rc;
+    if (E == 0) return ENS_OK;
+    if (!rowptr || !colidx || !vals) return set_error(h, ENS_EINVAL, "ens_mg_setup: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ES = E * S;
+    for (int l = 1; l < w.L; l++) {
+        ens_problem pc = *p;
+        pc.n = w.lv[l].n;
+        rc = pattern_into(h, &pc, w.lv[l].rp, w.lv[l].ci, st);
+        if (rc) return rc;
+    }
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(w.bad, 0, sizeof(int) * ES, st));
+    for (int l = 0; l < w.L; l++) {
+        MgLevel &v = w.lv[l];
+        const int32_t *rp = l ? v.rp : rowptr, *ci = l ? v.ci : colidx;
+        const double *vl = l ? v.vals : vals;
+        if (l > 0) {
+            const MgLevel &f = w.lv[l - 1];
+            k_mg_galerkin<<<rl_grid(v.J, S, E), kBlock, 0, st>>>(f.n, v.n, S, l - 1 ? f.rp : rowptr,
+                                                                 l - 1 ? f.vals : vals, v.rp, v.ci, v.vals);
+        }
+        ENS_CUDA_CHECK(h, cudaMemsetAsync(v.lmax, 0, sizeof(unsigned long long) * ES, st));
+        k_mg_diag<<<rl_grid(v.J, S, E), kBlock, 0, st>>>(v.J, S, rp, ci, vl, v.dinv, v.lmax, w.bad);
+        k_mg_coef<<<(ES + kBlock - 1) / kBlock, kBlock, 0, st>>>(ES, v.lmax, v.coef);
+    }
+    {
+        const MgLevel &c = w.lv[w.L - 1];
+        k_mg_chol<<<dim3((unsigned)S, (unsigned)E), 32, 0, st>>>(S, w.L > 1 ? c.rp : rowptr, w.L > 1 ? c.ci : colidx,
+                                                                  w.L > 1 ? c.vals : vals, w.cinv, w.bad);
+    }
+    ENS_LAUNCH_CHECK(h, "ens_mg_setup");
+    return ENS_OK;
+}
+
+extern "C" int ens_mg_level(ens_handle h, const ens_problem *p, int S, int E, int level, double *vals_out,
+                            double *lmax_out, const void *work, size_t work_bytes, void *stream)
+{
+    MgWork w;
+    int rc = mg_check(h, "ens_mg_level", p, S, E, work, work_bytes, &w);
+    if (rc) return rc;
+    if (level < 0 || level >= w.L) return set_error(h, ENS_EINVAL, "ens_mg_level: no such level");
+    if (E == 0) return ENS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const MgLevel &v = w.lv[level];
+    const size_t ES = (size_t)E * S;
+    if (vals_out && level > 0)
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(vals_out, v.vals, ES * v.nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (lmax_out)
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(lmax_out, v.lmax, ES * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return ENS_OK;
+}
+
+extern "C" int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+                            const int32_t *colidx, const double *vals, const double *r, double *z, void *work,
+                            size_t work_bytes, void *stream)
+{
+    MgWork w;
+    int rc = mg_check(h, "ens_mg_apply", p, S, E, work, work_bytes, &w);
+    if (rc) return rc;
+    if (E == 0) return ENS_OK;
+    if (!rowptr || !colidx || !vals || !r || !z) return set_error(h, ENS_EINVAL, "ens_mg_apply: null pointer");
+    return mg_vcycle(h, w, rowptr, colidx, vals, S, E, r, z, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+                               const int32_t *colidx, const double *vals, const double *b, double *x,
+                               const uint8_t *active, double rtol, int maxit, int32_t *iters, double *relres,
+                               int32_t *status, void *work, size_t work_bytes, void *stream)
+{
+    MgWork w;
+    int rc = mg_check(h, "ens_mgpcg_solve", p, S, E, work, work_bytes, &w);
+    if (rc) return rc;
+    if (E == 0) return ENS_OK;
+    if (!rowptr || !colidx || !vals || !b || !x || !iters || !relres || !status)
+        return set_error(h, ENS_EINVAL, "ens_mgpcg_solve: null pointer");
+    if (!(rtol >= 0.0)) return set_error(h, ENS_EINVAL, "ens_mgpcg_solve: rtol must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int J = w.lv[0].J;
+    CgArgs a;
+    a.J = J; a.S = S; a.E = E; a.nblk = w.nblk; a.maxit = maxit; a.rtol = rtol;
+    a.active = active; a.iters = iters; a.status = status; a.relres = relres;
+    const dim3 gred((unsigned)w.nblk, (unsigned)E), grl = rl_grid(J, S, E);
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(w.live_total, 0, sizeof(int), st));
+    // x = 0, r = b, z = M r, p = z; b^T b and r^T z decide each lane's start
+    k_mgcg_init<<<gred, kBlock, 0, st>>>(J, S, w.nblk, b, x, w.r, w.part0);
+    rc = mg_vcycle(h, w, rowptr, colidx, vals, S, E, w.r, w.z, nullptr, st);
+    if (rc) return rc;
+    k_mgcg_dot<<<gred, kBlock, 0, st>>>(J, S, w.nblk, w.r, w.z, nullptr, nullptr, w.part1);
+    k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_INIT, w.part0, w.part1, w);
+    k_mgcg_dir<<<grl, kBlock, 0, st>>>(J, S, w.z, w.p, nullptr, w.live, nullptr);
+    ENS_LAUNCH_CHECK(h, "ens_mgpcg_solve: init");
+    int left = 0;
+    ENS_CUDA_CHECK(h, cudaMemcpyAsync(&left, w.live_total, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+    int trips = 0;
+    while (left > 0 && trips < maxit) {
+        // a few iterations per look at the live count: a lane freezes at its
+        // own iteration, so the count only decides when launching can stop
+        const int chunk = trips < 8 ? 2 : 4;
+        for (int c = 0; c < chunk && trips < maxit; c++, trips++) {
+            k_mgcg_spmv<<<grl, kBlock, 0, st>>>(J, S, rowptr, colidx, vals, w.p, w.q, w.live, w.ens_live);
+            k_mgcg_dot<<<gred, kBlock, 0, st>>>(J, S, w.nblk, w.p, w.q, w.live, w.ens_live, w.part0);
+            k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_ALPHA, w.part0, nullptr, w);
+            k_mgcg_update<<<gred, kBlock, 0, st>>>(J, S, w.nblk, x, w.r, w.p, w.q, w.alpha, w.live, w.ens_live,
+                                                   w.part0);
+            k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_CONV, w.part0, nullptr, w);
+            rc = mg_vcycle(h, w, rowptr, colidx, vals, S, E, w.r, w.z, w.ens_live, st);
+            if (rc) return rc;
+            k_mgcg_dot<<<gred, kBlock, 0, st>>>(J, S, w.nblk, w.r, w.z, w.live, w.ens_live, w.part0);
+            k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_BETA, w.part0, nullptr, w);
+            k_mgcg_dir<<<grl, kBlock, 0, st>>>(J, S, w.z, w.p, w.beta, w.live, w.ens_live);
+        }
+        ENS_LAUNCH_CHECK(h, "ens_mgpcg_solve: iteration");
+        ENS_CUDA_CHECK(h, cudaMemcpyAsync(&left, w.live_total, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ENS_CUDA_CHECK(h, cudaStreamSynchronize(st));
+    }
+    return ENS_OK;
+}

@@ -26,7 +26,8 @@ EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "e
            "ens_sg_refine", "ens_sg_initial", "ens_sg_eval", "ens_qoi", "ens_spmv",
            "ens_pcg_solve_static", "ens_pcg_ir_workspace_size", "ens_pcg_solve_ir",
            "ens_adjoint_workspace_size", "ens_adjoint_grad", "ens_param_indicator",
-           "ens_stream_workspace_size", "ens_solve_stream", "ens_pcg_branches", "ens_check_pattern")
+           "ens_stream_workspace_size", "ens_solve_stream", "ens_pcg_branches", "ens_check_pattern",
+           "ens_mg_workspace_size", "ens_mg_setup", "ens_mg_level", "ens_mg_apply", "ens_mgpcg_solve")
 
 _lib = None
 _lock = threading.Lock()
@@ -87,6 +88,13 @@ def _declare(L):
     L.ens_solve_stream.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, vp, vp, vp, c.c_double,
                                    c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
     L.ens_param_indicator.argtypes = [vp, c.POINTER(Problem), c.c_int, vp, vp, vp]
+    L.ens_mg_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
+    L.ens_mg_workspace_size.restype = c.c_size_t
+    L.ens_mg_setup.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_mg_level.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, vp, vp, vp, c.c_size_t, vp]
+    L.ens_mg_apply.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_mgpcg_solve.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, c.c_double,
+                                  c.c_int, vp, vp, vp, vp, c.c_size_t, vp]
     L.ens_adjoint_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
     L.ens_adjoint_workspace_size.restype = c.c_size_t
     L.ens_adjoint_grad.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
@@ -253,6 +261,68 @@ def ens_spmv(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx, vals, 
     rc = load().ens_spmv(h.ptr, int(J), int(nnz), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
                          _ptr(p), _ptr(q), _ptr(pq), _ptr(work), work.numel(), _stream(stream))
     h.check(rc, "ens_spmv")
+
+
+def ens_mg_workspace_size(prob: Problem, S: int, E: int) -> int:
+    """Bytes of workspace of the multigrid calls (0 when the problem has no hierarchy)."""
+    return int(load().ens_mg_workspace_size(ctypes.byref(prob), int(S), int(E)))
+
+
+def _mg_sizes(prob, S, E, vals, work):
+    J, nnz = ens_problem_size(prob)
+    _check_dtype(vals, torch.float64, "vals")
+    if vals.numel() != E * nnz * S:
+        raise ValueError("vals size does not match E, nnz, S")
+    if work.dtype != torch.uint8:
+        raise TypeError("work must be a uint8 tensor")
+    return J, nnz
+
+
+def ens_mg_setup(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, vals, work, stream=None):
+    """Build the per-sample multigrid hierarchy of the fine values into work."""
+    _mg_sizes(prob, S, E, vals, work)
+    rc = load().ens_mg_setup(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                             _ptr(work), work.numel(), _stream(stream))
+    h.check(rc, "ens_mg_setup")
+
+
+def ens_mg_level(h: Handle, prob: Problem, S: int, E: int, level: int, vals_out, lmax_out, work, stream=None):
+    """Copy a level's Galerkin values [E][nnz_l][S] and Gershgorin bounds [E][S] out of work."""
+    for t, nm in ((vals_out, "vals_out"), (lmax_out, "lmax_out")):
+        if t is not None:
+            _check_dtype(t, torch.float64, nm)
+    rc = load().ens_mg_level(h.ptr, ctypes.byref(prob), int(S), int(E), int(level), _ptr(vals_out), _ptr(lmax_out),
+                             _ptr(work), work.numel(), _stream(stream))
+    h.check(rc, "ens_mg_level")
+
+
+def ens_mg_apply(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, vals, r, z, work, stream=None):
+    """z = one V-cycle applied to r (hierarchy of the last ens_mg_setup on work)."""
+    J, _ = _mg_sizes(prob, S, E, vals, work)
+    for t, nm in ((r, "r"), (z, "z")):
+        _check_dtype(t, torch.float64, nm)
+        if t.numel() != E * J * S:
+            raise ValueError(f"{nm} size does not match E, J, S")
+    rc = load().ens_mg_apply(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                             _ptr(r), _ptr(z), _ptr(work), work.numel(), _stream(stream))
+    h.check(rc, "ens_mg_apply")
+
+
+def ens_mgpcg_solve(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, vals, b, x, active, rtol: float,
+                    maxit: int, iters, relres, status, work, stream=None):
+    """Multigrid-preconditioned ensemble CG (after ens_mg_setup on work)."""
+    J, _ = _mg_sizes(prob, S, E, vals, work)
+    for t, nm, dt in ((b, "b", torch.float64), (x, "x", torch.float64), (iters, "iters", torch.int32),
+                      (relres, "relres", torch.float64), (status, "status", torch.int32)):
+        _check_dtype(t, dt, nm)
+    if active is not None:
+        _check_dtype(active, torch.uint8, "active")
+    if b.numel() != E * J * S or x.numel() != E * J * S or iters.numel() != E * S:
+        raise ValueError("array sizes do not match E, J, S")
+    rc = load().ens_mgpcg_solve(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                                _ptr(b), _ptr(x), _ptr(active), float(rtol), int(maxit), _ptr(iters), _ptr(relres),
+                                _ptr(status), _ptr(work), work.numel(), _stream(stream))
+    h.check(rc, "ens_mgpcg_solve")
 
 
 def ens_pcg_ir_workspace_size(J: int, nnz: int, S: int, E: int) -> int:

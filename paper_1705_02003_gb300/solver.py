@@ -17,10 +17,16 @@ from . import ens
 
 
 class EnsembleSolver:
+    """precond = "jacobi" (ens_pcg_solve) or "mg" (ens_mg_setup + ens_mgpcg_solve:
+    the multigrid V-cycle of the trilinear problems)."""
+
     def __init__(self, handle: ens.Handle, prob: ens.Problem, S: int, max_samples: int, rtol: float,
-                 maxit: int, device=None):
+                 maxit: int, device=None, precond: str = "jacobi"):
+        if precond not in ("jacobi", "mg"):
+            raise ValueError(f"unknown preconditioner {precond}")
         self.h = handle
         self.prob = prob
+        self.precond = precond
         self.S = int(S)
         self.N = prob.nparam
         self.rtol = float(rtol)
@@ -44,8 +50,13 @@ class EnsembleSolver:
         self.status = torch.empty(lanes, dtype=torch.int32, device=dev)
         self.relres = torch.empty(lanes, **f64)
         self.qoi = torch.empty(lanes, **f64)
-        self.work = torch.empty(ens.ens_pcg_workspace_size(self.J, self.nnz, self.S, self.Emax),
-                                dtype=torch.uint8, device=dev)
+        if precond == "mg":
+            need = ens.ens_mg_workspace_size(prob, self.S, self.Emax)
+            if need == 0:
+                raise ValueError("this problem has no multigrid hierarchy (trilinear problems, n = 2^k - 1)")
+        else:
+            need = ens.ens_pcg_workspace_size(self.J, self.nnz, self.S, self.Emax)
+        self.work = torch.empty(need, dtype=torch.uint8, device=dev)
 
     def bytes_per_iteration(self, E: int) -> int:
         """Algorithmic bytes of one PCG iteration of E ensembles: values, graph,
@@ -80,8 +91,13 @@ class EnsembleSolver:
         b = self.b[: E * J * S]
         x = self.x[: E * J * S]
         ens.ens_assemble(self.h, self.prob, S, E, self.xi[: L * self.N], self.rowptr, self.colidx, vals, dinv, b)
-        ens.ens_pcg_solve(self.h, J, nnz, S, E, self.rowptr, self.colidx, vals, dinv, b, x, act, self.rtol,
-                          self.maxit, self.iters[:L], self.relres[:L], self.status[:L], self.work)
+        if self.precond == "mg":
+            ens.ens_mg_setup(self.h, self.prob, S, E, self.rowptr, self.colidx, vals, self.work)
+            ens.ens_mgpcg_solve(self.h, self.prob, S, E, self.rowptr, self.colidx, vals, b, x, act, self.rtol,
+                                self.maxit, self.iters[:L], self.relres[:L], self.status[:L], self.work)
+        else:
+            ens.ens_pcg_solve(self.h, J, nnz, S, E, self.rowptr, self.colidx, vals, dinv, b, x, act, self.rtol,
+                              self.maxit, self.iters[:L], self.relres[:L], self.status[:L], self.work)
         ens.ens_qoi(self.h, J, S, E, x, self.qoi[:L], w=weights)
         return self.iters[:M], self.status[:M], self.relres[:M], self.qoi[:M]
 

@@ -103,7 +103,7 @@ class Adaptive:
 
     def __init__(self, handle: ens.Handle, wl: inputs.Workload, S: int | None = None,
                  solver: EnsembleSolver | None = None, per_sample: bool = False, repack: bool = False,
-                 chunk: int = 64):
+                 chunk: int = 64, precond: str = "jacobi"):
         self.h = handle
         self.wl = wl
         self.S = wl.S if S is None else S
@@ -112,7 +112,9 @@ class Adaptive:
         cap = min(wl.n_max, 16384)
         if solver is None:
             solver = EnsembleSolver(handle, self.prob, 1 if per_sample else self.S,
-                                    1 if per_sample else cap, wl.rtol, wl.maxit)
+                                    1 if per_sample else cap, wl.rtol, wl.maxit, precond=precond)
+        if repack and solver.precond != "jacobi":
+            raise ValueError("lane re-packing runs the Jacobi solver")
         self.solver = solver
         self.dev = solver.dev
         self.launches = 0

@@ -122,7 +122,7 @@ def test_entry_points_refuse_null_arguments_without_crashing():
     L = ens.load()
     skip = {"ens_create", "ens_last_error", "ens_problem_size", "ens_pcg_workspace_size",
             "ens_pcg_ir_workspace_size", "ens_stream_workspace_size", "ens_adjoint_workspace_size",
-            "ens_sg_refine", "ens_sg_initial"}
+            "ens_sg_refine", "ens_sg_initial", "ens_mg_workspace_size"}
     for name in ens.EXPORTS:
         if name in skip:
             continue
@@ -140,3 +140,18 @@ def test_entry_points_refuse_null_arguments_without_crashing():
             assert rc == 0
         else:
             assert rc < 0, name
+
+
+def test_multigrid_workspace_only_for_the_trilinear_hierarchies():
+    """The hierarchy exists for the trilinear problems with n = 2^k - 1; the
+    size grows with the ensembles and is 0 (unsupported) otherwise."""
+    f = ens.ens_mg_workspace_size
+    a = f(ens.problem("q1_3d_kl", 31, 4, 0.0), 16, 2)
+    assert a > 0 and f(ens.problem("q1_3d_disc", 31, 4, 0.0), 16, 2) == a
+    assert f(ens.problem("q1_3d_kl", 31, 4, 0.0), 16, 4) > a
+    assert f(ens.problem("q1_3d_kl", 15, 4, 0.0), 16, 2) < a
+    assert f(ens.problem("q1_3d_kl", 3, 4, 0.0), 1, 1) > 0
+    for bad in (ens.problem("q1_3d_kl", 30, 4, 0.0), ens.problem("q1_3d_kl", 16, 4, 0.0),
+                ens.problem("fd7", 31, 6, 3.0), ens.problem("q1", 31, 4, 4.0)):
+        assert f(bad, 16, 2) == 0
+    assert f(ens.problem("q1_3d_kl", 31, 4, 0.0), 3, 2) == 0  # S must be a power of two

@@ -216,13 +216,25 @@ __device__ __forceinline__ double w1(int f, int c)
     return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0);
 }
 
+// a * 2^-m, exactly: the weights w_i w_j are powers of two, so their product
+// with a only lowers a's exponent (an integer subtraction on the bits) unless
+// the result would leave the normal range, where the multiply itself is used.
+__device__ __forceinline__ double scale_pow2(double a, int m)
+{
+    const long long bits = __double_as_longlong(a);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    if (ex > m && ex != 0x7ff) return __longlong_as_double(bits - ((long long)m << 52));
+    return dmul(a, 1.0 / (double)(1 << m));
+}
+
 // A_c = P^T A_f P for every coarse row-lane, one coarse entry (I, J) at a
 // time: its contributions w_i w_j a_ij are added in the order of the triple
 // sum (fine nodes i of I ascending, then the columns j of row i ascending,
-// restricted to the children of J), each product and sum rounded on its own;
-// the weights are powers of two, so the products are exact.  Row i's columns
-// are its 3x3x3 neighbourhood clipped to the grid, in lexicographic order, so
-// the position of column j in the row follows from the clipped box.
+// restricted to the children of J), each sum rounded on its own; the products
+// are exact (powers of two), so the entry equals the textbook triple sum with
+// separate roundings bit for bit.  Row i's columns are its 3x3x3 neighbourhood
+// clipped to the grid, in lexicographic order, so the position of column j in
+// the row follows from the clipped box.
 __global__ void k_mg_galerkin(int nf, int nc, int S, const int32_t *__restrict__ rpf, const double *__restrict__ vf,
                               const int32_t *__restrict__ rpc, const int32_t *__restrict__ cic,
                               double *__restrict__ vc)
@@ -251,14 +263,15 @@ __global__ void k_mg_galerkin(int nf, int nc, int S, const int32_t *__restrict__
                     const int lo2 = max(rb2, 2 * J2), hi2 = min(i2 + 1, min(nf - 1, 2 * J2 + 2));
                     if (lo0 > hi0 || lo1 > hi1 || lo2 > hi2) continue;
                     const int i = i0 + nf * (i1 + nf * i2);
-                    const double wi = dmul(dmul(w1(i0, I0), w1(i1, I1)), w1(i2, I2));
+                    // half weights of i (w_i = 2^-mi) and of the j below (w_j = 2^-mj)
+                    const int mi = (i0 != 2 * I0 + 1) + (i1 != 2 * I1 + 1) + (i2 != 2 * I2 + 1);
                     const int base = rpf[i];
                     for (int j2 = lo2; j2 <= hi2; j2++)
                         for (int j1 = lo1; j1 <= hi1; j1++)
                             for (int j0 = lo0; j0 <= hi0; j0++) {
                                 const int k = base + ((j2 - rb2) * rn1 + (j1 - rb1)) * rn0 + (j0 - rb0);
-                                const double wj = dmul(dmul(w1(j0, J0), w1(j1, J1)), w1(j2, J2));
-                                acc = dadd(acc, dmul(dmul(wi, wj), v[(size_t)k * S]));
+                                const int mj = (j0 != 2 * J0 + 1) + (j1 != 2 * J1 + 1) + (j2 != 2 * J2 + 1);
+                                acc = dadd(acc, scale_pow2(v[(size_t)k * S], mi + mj));
                             }
                 }
         out[(size_t)kc * S] = acc;

@@ -218,64 +218,73 @@ __device__ __forceinline__ double w1(int f, int c)
 
 // a * 2^-m, exactly: the weights w_i w_j are powers of two, so their product
 // with a only lowers a's exponent (an integer subtraction on the bits) unless
-// the result would leave the normal range, where the multiply itself is used.
+// the result would leave the normal range (zero, subnormal, infinite or NaN
+// values), where the multiply itself is used.  That rare case is a separate
+// call, so the multiply is not executed (predicated) for every term: as an
+// inline branch it doubled the kernel's FP64 instructions (Nsight Compute).
+__device__ __noinline__ double scale_pow2_slow(double a, int m)
+{
+    return dmul(a, __longlong_as_double((long long)(1023 - m) << 52));
+}
+
 __device__ __forceinline__ double scale_pow2(double a, int m)
 {
     const long long bits = __double_as_longlong(a);
     const int ex = (int)((bits >> 52) & 0x7ff);
     if (ex > m && ex != 0x7ff) return __longlong_as_double(bits - ((long long)m << 52));
-    return dmul(a, 1.0 / (double)(1 << m));
+    return scale_pow2_slow(a, m);
 }
 
-// A_c = P^T A_f P for every coarse row-lane, one coarse entry (I, J) at a
-// time: its contributions w_i w_j a_ij are added in the order of the triple
-// sum (fine nodes i of I ascending, then the columns j of row i ascending,
-// restricted to the children of J), each sum rounded on its own; the products
-// are exact (powers of two), so the entry equals the textbook triple sum with
-// separate roundings bit for bit.  Row i's columns are its 3x3x3 neighbourhood
-// clipped to the grid, in lexicographic order, so the position of column j in
-// the row follows from the clipped box.
+// A_c = P^T A_f P, one thread per coarse entry (I, J) and lane: its
+// contributions w_i w_j a_ij are added in the order of the triple sum (fine
+// nodes i of I ascending, then the columns j of row i ascending, restricted to
+// the children of J), each sum rounded on its own; the products are exact
+// (powers of two), so the entry equals the textbook triple sum with separate
+// roundings bit for bit.  A row's columns (fine or coarse) are its 3x3x3
+// neighbourhood clipped to the grid, in lexicographic order, so the position
+// of a column in its row follows from the clipped box.
 __global__ void k_mg_galerkin(int nf, int nc, int S, const int32_t *__restrict__ rpf, const double *__restrict__ vf,
-                              const int32_t *__restrict__ rpc, const int32_t *__restrict__ cic,
-                              double *__restrict__ vc)
+                              const int32_t *__restrict__ rpc, double *__restrict__ vc)
 {
-    int s, I;
-    row_lane(S, &s, &I);
+    int s, q;
+    row_lane(S, &s, &q);  // q = 27 I + slot
     const int e = blockIdx.y;
     const int Jc = nc * nc * nc, Jf = nf * nf * nf;
-    if (I >= Jc) return;
+    if (q >= 27 * Jc) return;
+    const int I = q / 27, slot = q % 27;
     const int I0 = I % nc, I1 = (I / nc) % nc, I2 = I / (nc * nc);
+    const int J0 = I0 + slot % 3 - 1, J1 = I1 + (slot / 3) % 3 - 1, J2 = I2 + slot / 9 - 1;
+    if (J0 < 0 || J0 >= nc || J1 < 0 || J1 >= nc || J2 < 0 || J2 >= nc) return;
     const int64_t nnzf = rpf[Jf], nnzc = rpc[Jc];
     const double *v = vf + (size_t)e * nnzf * S + s;
-    double *out = vc + (size_t)e * nnzc * S + s;
-    for (int kc = rpc[I]; kc < rpc[I + 1]; kc++) {
-        const int Jn = cic[kc];
-        const int J0 = Jn % nc, J1 = (Jn / nc) % nc, J2 = Jn / (nc * nc);
-        double acc = 0.0;
-        for (int i2 = 2 * I2; i2 <= 2 * I2 + 2; i2++)
-            for (int i1 = 2 * I1; i1 <= 2 * I1 + 2; i1++)
-                for (int i0 = 2 * I0; i0 <= 2 * I0 + 2; i0++) {
-                    // row box of i and the children box of J, per axis
-                    const int rb0 = max(i0 - 1, 0), rb1 = max(i1 - 1, 0), rb2 = max(i2 - 1, 0);
-                    const int rn0 = min(i0 + 1, nf - 1) - rb0 + 1, rn1 = min(i1 + 1, nf - 1) - rb1 + 1;
-                    const int lo0 = max(rb0, 2 * J0), hi0 = min(i0 + 1, min(nf - 1, 2 * J0 + 2));
-                    const int lo1 = max(rb1, 2 * J1), hi1 = min(i1 + 1, min(nf - 1, 2 * J1 + 2));
-                    const int lo2 = max(rb2, 2 * J2), hi2 = min(i2 + 1, min(nf - 1, 2 * J2 + 2));
-                    if (lo0 > hi0 || lo1 > hi1 || lo2 > hi2) continue;
-                    const int i = i0 + nf * (i1 + nf * i2);
-                    // half weights of i (w_i = 2^-mi) and of the j below (w_j = 2^-mj)
-                    const int mi = (i0 != 2 * I0 + 1) + (i1 != 2 * I1 + 1) + (i2 != 2 * I2 + 1);
-                    const int base = rpf[i];
-                    for (int j2 = lo2; j2 <= hi2; j2++)
-                        for (int j1 = lo1; j1 <= hi1; j1++)
-                            for (int j0 = lo0; j0 <= hi0; j0++) {
-                                const int k = base + ((j2 - rb2) * rn1 + (j1 - rb1)) * rn0 + (j0 - rb0);
-                                const int mj = (j0 != 2 * J0 + 1) + (j1 != 2 * J1 + 1) + (j2 != 2 * J2 + 1);
-                                acc = dadd(acc, scale_pow2(v[(size_t)k * S], mi + mj));
-                            }
-                }
-        out[(size_t)kc * S] = acc;
-    }
+    double acc = 0.0;
+    for (int i2 = 2 * I2; i2 <= 2 * I2 + 2; i2++)
+        for (int i1 = 2 * I1; i1 <= 2 * I1 + 2; i1++)
+            for (int i0 = 2 * I0; i0 <= 2 * I0 + 2; i0++) {
+                // row box of i and the children box of J, per axis
+                const int rb0 = max(i0 - 1, 0), rb1 = max(i1 - 1, 0), rb2 = max(i2 - 1, 0);
+                const int rn0 = min(i0 + 1, nf - 1) - rb0 + 1, rn1 = min(i1 + 1, nf - 1) - rb1 + 1;
+                const int lo0 = max(rb0, 2 * J0), hi0 = min(i0 + 1, min(nf - 1, 2 * J0 + 2));
+                const int lo1 = max(rb1, 2 * J1), hi1 = min(i1 + 1, min(nf - 1, 2 * J1 + 2));
+                const int lo2 = max(rb2, 2 * J2), hi2 = min(i2 + 1, min(nf - 1, 2 * J2 + 2));
+                if (lo0 > hi0 || lo1 > hi1 || lo2 > hi2) continue;
+                const int i = i0 + nf * (i1 + nf * i2);
+                // half weights of i (w_i = 2^-mi) and of the j below (w_j = 2^-mj)
+                const int mi = (i0 != 2 * I0 + 1) + (i1 != 2 * I1 + 1) + (i2 != 2 * I2 + 1);
+                const int base = rpf[i];
+                for (int j2 = lo2; j2 <= hi2; j2++)
+                    for (int j1 = lo1; j1 <= hi1; j1++)
+                        for (int j0 = lo0; j0 <= hi0; j0++) {
+                            const int k = base + ((j2 - rb2) * rn1 + (j1 - rb1)) * rn0 + (j0 - rb0);
+                            const int mj = (j0 != 2 * J0 + 1) + (j1 != 2 * J1 + 1) + (j2 != 2 * J2 + 1);
+                            acc = dadd(acc, scale_pow2(v[(size_t)k * S], mi + mj));
+                        }
+            }
+    // the entry's position in coarse row I
+    const int cb0 = max(I0 - 1, 0), cb1 = max(I1 - 1, 0), cb2 = max(I2 - 1, 0);
+    const int cn0 = min(I0 + 1, nc - 1) - cb0 + 1, cn1 = min(I1 + 1, nc - 1) - cb1 + 1;
+    const int kc = rpc[I] + ((J2 - cb2) * cn1 + (J1 - cb1)) * cn0 + (J0 - cb0);
+    vc[((size_t)e * nnzc + kc) * S + s] = acc;
 }
 
 // The coarsest level (27 unknowns), one block per lane: Cholesky A = L L^T in
@@ -799,8 +808,8 @@ extern "C" int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, co
         const double *vl = l ? v.vals : vals;
         if (l > 0) {
             const MgLevel &f = w.lv[l - 1];
-            k_mg_galerkin<<<rl_grid(v.J, S, E), kBlock, 0, st>>>(f.n, v.n, S, l - 1 ? f.rp : rowptr,
-                                                                 l - 1 ? f.vals : vals, v.rp, v.ci, v.vals);
+            k_mg_galerkin<<<rl_grid(27 * v.J, S, E), kBlock, 0, st>>>(f.n, v.n, S, l - 1 ? f.rp : rowptr,
+                                                                      l - 1 ? f.vals : vals, v.rp, v.vals);
         }
         ENS_CUDA_CHECK(h, cudaMemsetAsync(v.lmax, 0, sizeof(unsigned long long) * ES, st));
         k_mg_diag<<<rl_grid(v.J, S, E), kBlock, 0, st>>>(v.J, S, rp, ci, vl, v.dinv, v.lmax, w.bad);

@@ -208,8 +208,9 @@ int ens_mg_level(ens_handle h, const ens_problem *p, int S, int E, int level, do
                  double *lmax_out, const void *work, size_t work_bytes, void *stream);
 
 /* z[E][J][S] = one V-cycle applied to r[E][J][S] (device f64) with the
- * hierarchy of the last ens_mg_setup on `work` (same vals).  Lanes marked
- * unusable get undefined values.  No synchronisation. */
+ * hierarchy of the last ens_mg_setup on `work` (same p, S, E and vals: the
+ * workspace layout depends on them).  Lanes marked unusable get undefined
+ * values.  No synchronisation. */
 int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
                  const int32_t *colidx, const double *vals, const double *r, double *z,
                  void *work, size_t work_bytes, void *stream);
@@ -218,7 +219,7 @@ int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, const int32_t
  * outputs of ens_pcg_solve (x = 0 start, per-sample inner products, the
  * unpreconditioned ||r_s|| <= rtol ||b_s|| test after each update, frozen lanes,
  * status codes; active may be NULL).  Needs ens_mg_setup on `work` with the
- * same vals first.  The host launches the iterations and reads the live-lane
+ * same p, S, E and vals first.  The host launches the iterations and reads the live-lane
  * count back every two to four of them (the call synchronises the stream);
  * each lane still stops at its own iteration, so results do not depend on that
  * cadence.  Deterministic: per-lane results depend only on the lane's data, S

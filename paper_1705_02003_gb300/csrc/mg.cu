@@ -19,10 +19,10 @@
 //     explicit inverse built from it;
 //   - one V-cycle per CG iteration (pre-smooth from 0, restrict, recurse,
 //     prolong-add, post-smooth).
-// The setup (Galerkin products, Gershgorin bounds, Cholesky) rounds every
-// product and sum on its own in the order of the textbook triple sum, so it
-// reproduces a plain host computation bit for bit; the V-cycle itself uses
-// fused multiply-adds.
+// The setup (Galerkin products, Gershgorin bounds, Cholesky) follows the order
+// of the textbook sums and rounds each sum on its own (the Galerkin products by
+// the power-of-two weights are exact), so it reproduces a plain host
+// computation bit for bit; the V-cycle itself uses fused multiply-adds.
 //
 // Layout: every vector of level l is [E][J_l][S] f64, every matrix
 // [E][nnz_l][S] f64 (level 0 is the caller's), the coarsest operator's
@@ -216,31 +216,17 @@ __device__ __forceinline__ double w1(int f, int c)
     return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0);
 }
 
-// a * 2^-m, exactly: the weights w_i w_j are powers of two, so their product
-// with a only lowers a's exponent (an integer subtraction on the bits) unless
-// the result would leave the normal range (zero, subnormal, infinite or NaN
-// values), where the multiply itself is used.  That rare case is a separate
-// call, so the multiply is not executed (predicated) for every term: as an
-// inline branch it doubled the kernel's FP64 instructions (Nsight Compute).
-__device__ __noinline__ double scale_pow2_slow(double a, int m)
-{
-    return dmul(a, __longlong_as_double((long long)(1023 - m) << 52));
-}
-
-__device__ __forceinline__ double scale_pow2(double a, int m)
-{
-    const long long bits = __double_as_longlong(a);
-    const int ex = (int)((bits >> 52) & 0x7ff);
-    if (ex > m && ex != 0x7ff) return __longlong_as_double(bits - ((long long)m << 52));
-    return scale_pow2_slow(a, m);
-}
+// 2^-m as a double (0 <= m <= 6), built from its exponent bits.
+__device__ __forceinline__ double pow2_neg(int m) { return __longlong_as_double((long long)(1023 - m) << 52); }
 
 // A_c = P^T A_f P, one thread per coarse entry (I, J) and lane: its
 // contributions w_i w_j a_ij are added in the order of the triple sum (fine
 // nodes i of I ascending, then the columns j of row i ascending, restricted to
-// the children of J), each sum rounded on its own; the products are exact
-// (powers of two), so the entry equals the textbook triple sum with separate
-// roundings bit for bit.  A row's columns (fine or coarse) are its 3x3x3
+// the children of J).  w_i w_j = 2^-m is exact, and so is its product with a
+// (normal) value, so a fused multiply-add rounds exactly what the textbook
+// triple sum with a separate product and sum rounds: the entry matches it bit
+// for bit.  (The product as a separate FP64 multiply, or as an exponent shift
+// with a rare-case branch, ran at half this kernel's speed or less.)  A row's columns (fine or coarse) are its 3x3x3
 // neighbourhood clipped to the grid, in lexicographic order, so the position
 // of a column in its row follows from the clipped box.
 __global__ void k_mg_galerkin(int nf, int nc, int S, const int32_t *__restrict__ rpf, const double *__restrict__ vf,
@@ -277,7 +263,7 @@ __global__ void k_mg_galerkin(int nf, int nc, int S, const int32_t *__restrict__
                         for (int j0 = lo0; j0 <= hi0; j0++) {
                             const int k = base + ((j2 - rb2) * rn1 + (j1 - rb1)) * rn0 + (j0 - rb0);
                             const int mj = (j0 != 2 * J0 + 1) + (j1 != 2 * J1 + 1) + (j2 != 2 * J2 + 1);
-                            acc = dadd(acc, scale_pow2(v[(size_t)k * S], mi + mj));
+                            acc = fma(v[(size_t)k * S], pow2_neg(mi + mj), acc);
                         }
             }
     // the entry's position in coarse row I

@@ -106,12 +106,15 @@ def test_gershgorin_bound():
     assert np.isnan(O.gershgorin(rp, ci, bad))
 
 
-def test_chebyshev_smoother_applies_the_chebyshev_polynomial():
+@pytest.mark.parametrize("tensor", [(1.0, 1.0, 1.0), (1.1, 1.0, 1.0), (7.0, 0.5, 2.0)])
+def test_chebyshev_smoother_applies_the_chebyshev_polynomial(tensor):
     """On A x = 0 from an eigenvector v of D^-1 A (constant diagonal: the tensor
-    sines), the smoother returns p(mu) v with p(t) = T_2((theta - t)/delta) / T_2(theta/delta)."""
+    sines), the smoother returns p(mu) v with p(t) = T_2((theta - t)/delta) / T_2(theta/delta).
+    diag(1.1, 1, 1) is the Section 4 field at y = 0."""
     n = 7
     h = 1.0 / (n + 1)
-    A = fem_3d(n)
+    ax, ay, az = tensor
+    A = fem_3d(n, ax, ay, az)
     rp, ci, v = in_pattern(n, A)
     dinv = 1.0 / np.diag(A)
     lmax = O.gershgorin(rp, ci, v)
@@ -124,8 +127,8 @@ def test_chebyshev_smoother_applies_the_chebyshev_polynomial():
         vec = np.einsum("l,j,i->lji", sz, sy, sx).ravel()
         kk = [(2 / h) * (1 - np.cos(w * np.pi * h)) for w in (k, m, q)]
         mm = [(h / 6) * (4 + 2 * np.cos(w * np.pi * h)) for w in (k, m, q)]
-        lam = kk[0] * mm[1] * mm[2] + mm[0] * kk[1] * mm[2] + mm[0] * mm[1] * kk[2]
-        np.testing.assert_allclose(A @ vec, lam * vec, atol=1e-12)
+        lam = ax * kk[0] * mm[1] * mm[2] + ay * mm[0] * kk[1] * mm[2] + az * mm[0] * mm[1] * kk[2]
+        np.testing.assert_allclose(A @ vec, lam * vec, atol=1e-12 * max(tensor))
         mu = lam * dinv[0]
         p = T2((theta - mu) / delta) / T2(theta / delta)
         out = O.cheb(rp, ci, v, dinv, lmax, np.zeros(n ** 3), vec)

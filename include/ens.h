@@ -1,6 +1,7 @@
 /*
  * ens.h -- C ABI of libens: ensemble Jacobi-PCG for parametrised anisotropic
- * diffusion on one GB300 (sm_103a), with surrogate-based ensemble grouping.
+ * diffusion on one GB300 (sm_103a), with surrogate-based ensemble grouping;
+ * for the 3-D trilinear problems also a multigrid-preconditioned ensemble CG.
  *
  * Method: D'Elia, Phipps, Rushdi, Ebeida, "Surrogate-based Ensemble Grouping
  * Strategies for Embedded Sampling-based Uncertainty Quantification"

@@ -2,6 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload q1_256_adaptive] [--no-arms] [--no-layers] [--no-paper] [--no-cpu]
+                    [--mixed-mg]
                     [--kernel-only [--kernel-ensembles E]]
 
 A step is one pass of the whole path over the workload: the grid-generation
@@ -26,6 +27,7 @@ The same run (one GPU) also reports:
   paper_tables    Section 4's Test 1 / Test 2 (32^3 trilinear FEM, N = 4), with
                   the Jacobi and the multigrid preconditioner: R_l, R,
                   measured and predicted speed-up for S = 4..32
+                  (--mixed-mg adds the multigrid solve with a float V-cycle)
   cpu_baseline    the CPU oracle on a bounded sample of the same points
 
 --kernel-only times K2 alone (the case the Nsight Compute summaries use).
@@ -320,6 +322,8 @@ def run_ours(args, wl):
     configs = {} if args.no_layers else run_configs(h, stream)
     pilot = {} if args.no_layers else run_pilot(h, stream)
     paper = {} if args.no_paper else run_paper(h, stream)
+    if args.mixed_mg:
+        paper["mixed_multigrid"] = run_mixed_mg(h, stream)
 
     # dominant kernel: the ensemble SpMV (K2) on a full-capacity batch
     sol = ad.solver
@@ -604,6 +608,32 @@ def run_paper(h, stream, S_list=(4, 8, 16, 32)):
     return out
 
 
+def run_mixed_mg(h, stream):
+    """The multigrid preconditioner with its V-cycle in float (CG in double)
+    against the FP64 V-cycle, on Section 4's Test 1 and Test 2: one full
+    adaptive grid each, surrogate grouping, S = 16; solve-call time, R and the
+    iteration counts (the grid is the same: it depends on G only)."""
+    from paper_1705_02003_gb300 import inputs
+    from paper_1705_02003_gb300.uq import Adaptive, ratios
+
+    out = {}
+    for name in ("q1_32c_test1", "q1_32c_test2"):
+        wl = inputs.WORKLOADS[name]
+        res = {}
+        for pc in ("mg", "mg32"):
+            ad = Adaptive(h, wl, S=16, precond=pc)
+            ad.run("sur")  # warm-up
+            ad.time_calls = True
+            r = ad.run("sur")
+            res[pc] = {"solve_ms": sum(ms for _, ms in ad.call_times()), "R": ratios(r)["run"][1],
+                       "iters_mean": float(r["I"].mean()), "iters_max": int(r["I"].max()), "I": r["I"]}
+            del ad
+        res["max_iter_diff"] = int(np.max(np.abs(res["mg32"].pop("I") - res["mg"].pop("I"))))
+        res["speedup_mg32_vs_mg"] = res["mg"]["solve_ms"] / res["mg32"]["solve_ms"]
+        out[name] = res
+    return out
+
+
 def run_layers(h, stream):
     """The three system layers on bounded samples of their workloads:
     FP32-in-FP64 refinement vs the FP64 solve on the 128^3 problem (one
@@ -787,6 +817,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-layers", action="store_true")
     ap.add_argument("--no-paper", action="store_true", help="skip the Section 4 tables (Test 1 / Test 2)")
+    ap.add_argument("--mixed-mg", action="store_true",
+                    help="also time the multigrid solve with its V-cycle in float on Test 1 / Test 2")
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--ref-samples", type=int, default=32)
     ap.add_argument("--kernel-only", action="store_true", help="time the ensemble SpMV alone (profiling)")

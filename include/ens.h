@@ -185,8 +185,16 @@ int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
  * level; one V-cycle (pre-smooth, coarse correction, post-smooth) per CG
  * iteration.  Other kinds or sizes: ENS_ENOTSUP / ENS_EINVAL. */
 
-/* Bytes of caller workspace the three calls below need (0 when unsupported). */
-size_t ens_mg_workspace_size(const ens_problem *p, int S, int E);
+/* Mixed precision (`mixed` = 1; 0 = FP64 throughout): the hierarchy is built
+ * in FP64 as described, then rounded once to float, and every V-cycle runs in
+ * float (r rounded in, z widened out); CG, its inner products, residual test
+ * and iterate stay FP64.  The preconditioner only approximates A^-1, so its
+ * rounding changes the iteration counts little (the FP32 and FP64 V-cycles
+ * differ by ~2e-7 relative).  Every call on one workspace uses the same p, S,
+ * E and `mixed` (the layout depends on them).
+ *
+ * Bytes of caller workspace the calls below need (0 when unsupported). */
+size_t ens_mg_workspace_size(const ens_problem *p, int S, int E, int mixed);
 
 /* Build the hierarchy of E ensembles from the fine values vals[E][nnz][S]
  * (device f64; rowptr/colidx the problem's graph from ens_pattern) into work:
@@ -197,7 +205,7 @@ size_t ens_mg_workspace_size(const ens_problem *p, int S, int E);
  * reports ENS_LANE_BADINPUT).  The products, sums and roots of the setup are
  * each rounded on their own, in the order of the definitions, so the coarse
  * values match a plain host computation bit for bit.  No synchronisation. */
-int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, int mixed, const int32_t *rowptr,
                  const int32_t *colidx, const double *vals, void *work, size_t work_bytes,
                  void *stream);
 
@@ -205,14 +213,14 @@ int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, const int32_t
  * values vals_out[E][nnz_l][S] (levels >= 1; level 0 is the caller's own) and
  * the Gershgorin bounds lmax_out[E][S] (0 for an unusable lane).  Either may
  * be NULL.  An inspection aid (no counterpart in the paper). */
-int ens_mg_level(ens_handle h, const ens_problem *p, int S, int E, int level, double *vals_out,
-                 double *lmax_out, const void *work, size_t work_bytes, void *stream);
+int ens_mg_level(ens_handle h, const ens_problem *p, int S, int E, int mixed, int level,
+                 double *vals_out, double *lmax_out, const void *work, size_t work_bytes, void *stream);
 
 /* z[E][J][S] = one V-cycle applied to r[E][J][S] (device f64) with the
  * hierarchy of the last ens_mg_setup on `work` (same p, S, E and vals: the
  * workspace layout depends on them).  Lanes marked unusable get undefined
  * values.  No synchronisation. */
-int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, int mixed, const int32_t *rowptr,
                  const int32_t *colidx, const double *vals, const double *r, double *z,
                  void *work, size_t work_bytes, void *stream);
 
@@ -225,7 +233,7 @@ int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, const int32_t
  * each lane still stops at its own iteration, so results do not depend on that
  * cadence.  Deterministic: per-lane results depend only on the lane's data, S
  * and J. */
-int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E, int mixed, const int32_t *rowptr,
                     const int32_t *colidx, const double *vals, const double *b, double *x,
                     const uint8_t *active, double rtol, int maxit, int32_t *iters, double *relres,
                     int32_t *status, void *work, size_t work_bytes, void *stream);

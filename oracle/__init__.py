@@ -100,6 +100,9 @@ def _declare(L):
     L.or_mg_apply.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, _f64p]
     L.or_mgpcg.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_int, _f64p,
                            c.POINTER(c.c_int), c.POINTER(c.c_double)]
+    L.or_mg_apply32.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, _f64p]
+    L.or_mgpcg32.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_int, _f64p,
+                             c.POINTER(c.c_int), c.POINTER(c.c_double)]
     L.or_solve_batch.argtypes = [c.c_int, c.c_int, c.c_int, c.c_double, c.c_int, _f64p, c.c_double,
                                  c.c_int, c.c_int, _i32p, _i32p, _f64p, _f64p, c.c_void_p]
     L.or_pcg_ir.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_double, c.c_int,
@@ -292,6 +295,24 @@ def mgpcg(n: int, rowptr, colidx, vals, b, rtol: float, maxit: int):
     rr = ctypes.c_double()
     st = lib().or_mgpcg(int(n), rowptr, colidx, _f64(vals), _f64(b), float(rtol), int(maxit), x,
                         ctypes.byref(it), ctypes.byref(rr))
+    return x, it.value, st, rr.value
+
+
+def mg_apply32(n: int, rowptr, colidx, vals, r):
+    """z = one V-cycle in float (hierarchy rounded to float) applied to r."""
+    z = np.zeros(n ** 3, np.float64)
+    if lib().or_mg_apply32(int(n), rowptr, colidx, _f64(vals), _f64(r), z):
+        raise ValueError("hierarchy setup failed")
+    return z
+
+
+def mgpcg32(n: int, rowptr, colidx, vals, b, rtol: float, maxit: int):
+    """CG (FP64) preconditioned by the float V-cycle. Returns (x, iters, status, relres)."""
+    x = np.zeros(n ** 3, np.float64)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().or_mgpcg32(int(n), rowptr, colidx, _f64(vals), _f64(b), float(rtol), int(maxit), x,
+                          ctypes.byref(it), ctypes.byref(rr))
     return x, it.value, st, rr.value
 
 

@@ -384,3 +384,205 @@ done:
     free(r); free(z); free(p); free(q);
     return status;
 }
+
+/* ---- FP32 V-cycle: the mixed-precision preconditioner ---------------------
+ * The hierarchy is built in FP64 as above, then its values, inverse diagonals
+ * and coarsest factor are rounded to float and one V-cycle runs entirely in
+ * float (the right-hand side rounded in, the correction widened out).  The
+ * Chebyshev coefficients are formed in FP64 and rounded: 1/theta, c1, c2 with
+ * d0 = D^-1 (b - A x) / theta and d1 = c1 d0 + c2 D^-1 (b - A x).  CG stays in
+ * FP64 (or_mgpcg32). */
+typedef struct {
+    float *v[OR_MG_MAXLEV], *dinv[OR_MG_MAXLEV];
+    float c[OR_MG_MAXLEV][3];
+    float *L;
+} mg32_t;
+
+static void mg32_from(const mg_t *m, mg32_t *f)
+{
+    for (int l = 0; l < m->nlev; l++) {
+        const int J = m->J[l];
+        const int64_t nnz = m->rp[l][J];
+        f->v[l] = malloc(sizeof(float) * nnz);
+        f->dinv[l] = malloc(sizeof(float) * J);
+        for (int64_t k = 0; k < nnz; k++) f->v[l][k] = (float)m->v[l][k];
+        for (int i = 0; i < J; i++) f->dinv[l][i] = (float)m->dinv[l][i];
+        const double lmax = m->lmax[l], lmin = lmax / MG_RATIO;
+        const double theta = (lmax + lmin) / 2.0, delta = (lmax - lmin) / 2.0;
+        const double sigma = theta / delta, rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
+        f->c[l][0] = (float)(1.0 / theta);
+        f->c[l][1] = (float)(rho1 * rho0);
+        f->c[l][2] = (float)(2.0 * rho1 / delta);
+    }
+    const int J = m->J[m->nlev - 1];
+    f->L = malloc(sizeof(float) * J * J);
+    for (int k = 0; k < J * J; k++) f->L[k] = (float)m->L[k];
+}
+
+static void mg32_free(const mg_t *m, mg32_t *f)
+{
+    for (int l = 0; l < m->nlev; l++) {
+        free(f->v[l]);
+        free(f->dinv[l]);
+    }
+    free(f->L);
+}
+
+static void spmv32(int J, const int64_t *rp, const int32_t *ci, const float *v, const float *x, float *y)
+{
+    for (int i = 0; i < J; i++) {
+        float s = 0.0f;
+        for (int64_t k = rp[i]; k < rp[i + 1]; k++) s = s + v[k] * x[ci[k]];
+        y[i] = s;
+    }
+}
+
+static void cheb32(int J, const int64_t *rp, const int32_t *ci, const float *v, const float *dinv, const float *c,
+                   const float *b, float *x)
+{
+    float *d = malloc(sizeof(float) * J), *ax = malloc(sizeof(float) * J);
+    spmv32(J, rp, ci, v, x, ax);
+    for (int i = 0; i < J; i++) {
+        d[i] = dinv[i] * (b[i] - ax[i]) * c[0];
+        x[i] = x[i] + d[i];
+    }
+    spmv32(J, rp, ci, v, x, ax);
+    for (int i = 0; i < J; i++) {
+        d[i] = c[1] * d[i] + c[2] * (dinv[i] * (b[i] - ax[i]));
+        x[i] = x[i] + d[i];
+    }
+    free(d);
+    free(ax);
+}
+
+static void vcycle32(const mg_t *m, const mg32_t *f, int l, const float *r, float *e)
+{
+    const int J = m->J[l];
+    if (l == m->nlev - 1) {
+        for (int i = 0; i < J; i++) {
+            float s = r[i];
+            for (int k = 0; k < i; k++) s = s - f->L[i * J + k] * e[k];
+            e[i] = s / f->L[i * J + i];
+        }
+        for (int i = J - 1; i >= 0; i--) {
+            float s = e[i];
+            for (int k = i + 1; k < J; k++) s = s - f->L[k * J + i] * e[k];
+            e[i] = s / f->L[i * J + i];
+        }
+        return;
+    }
+    const int nf = m->n[l], nc = m->n[l + 1], Jc = m->J[l + 1];
+    float *res = malloc(sizeof(float) * J), *rc = malloc(sizeof(float) * Jc), *ec = malloc(sizeof(float) * Jc);
+    for (int i = 0; i < J; i++) e[i] = 0.0f;
+    cheb32(J, m->rp[l], m->ci[l], f->v[l], f->dinv[l], f->c[l], r, e);
+    spmv32(J, m->rp[l], m->ci[l], f->v[l], e, res);
+    for (int i = 0; i < J; i++) res[i] = r[i] - res[i];
+    for (int c2 = 0; c2 < nc; c2++)  /* rc = P^T res */
+        for (int c1 = 0; c1 < nc; c1++)
+            for (int c0 = 0; c0 < nc; c0++) {
+                float acc = 0.0f;
+                for (int f2 = 2 * c2; f2 <= 2 * c2 + 2; f2++)
+                    for (int f1 = 2 * c1; f1 <= 2 * c1 + 2; f1++)
+                        for (int f0 = 2 * c0; f0 <= 2 * c0 + 2; f0++)
+                            acc = acc + (float)(w1(f0, c0) * w1(f1, c1) * w1(f2, c2)) * res[f0 + nf * f1 + nf * nf * f2];
+                rc[c0 + nc * c1 + nc * nc * c2] = acc;
+            }
+    vcycle32(m, f, l + 1, rc, ec);
+    for (int f2 = 0; f2 < nf; f2++)  /* e += P ec */
+        for (int f1 = 0; f1 < nf; f1++)
+            for (int f0 = 0; f0 < nf; f0++) {
+                float acc = 0.0f;
+                for (int c2 = (f2 - 1) / 2 - 1; c2 <= (f2 + 1) / 2; c2++)
+                    for (int c1 = (f1 - 1) / 2 - 1; c1 <= (f1 + 1) / 2; c1++)
+                        for (int c0 = (f0 - 1) / 2 - 1; c0 <= (f0 + 1) / 2; c0++) {
+                            if (c0 < 0 || c0 >= nc || c1 < 0 || c1 >= nc || c2 < 0 || c2 >= nc) continue;
+                            const double w = w1(f0, c0) * w1(f1, c1) * w1(f2, c2);
+                            if (w == 0.0) continue;
+                            acc = acc + (float)w * ec[c0 + nc * c1 + nc * nc * c2];
+                        }
+                e[f0 + nf * f1 + nf * nf * f2] = e[f0 + nf * f1 + nf * nf * f2] + acc;
+            }
+    cheb32(J, m->rp[l], m->ci[l], f->v[l], f->dinv[l], f->c[l], r, e);
+    free(res);
+    free(rc);
+    free(ec);
+}
+
+int or_mg_apply32(int n, const int64_t *rp, const int32_t *ci, const double *v, const double *r, double *z)
+{
+    mg_t m;
+    int rc = mg_build(n, rp, ci, v, &m);
+    if (rc == 0) {
+        mg32_t f;
+        mg32_from(&m, &f);
+        const int J = m.J[0];
+        float *r32 = malloc(sizeof(float) * J), *e32 = malloc(sizeof(float) * J);
+        for (int i = 0; i < J; i++) r32[i] = (float)r[i];
+        vcycle32(&m, &f, 0, r32, e32);
+        for (int i = 0; i < J; i++) z[i] = (double)e32[i];
+        free(r32);
+        free(e32);
+        mg32_free(&m, &f);
+    }
+    mg_free(&m);
+    return rc;
+}
+
+int or_mgpcg32(int n, const int64_t *rp, const int32_t *ci, const double *v, const double *b, double rtol,
+               int maxit, double *x, int *iters, double *relres)
+{
+    mg_t m;
+    mg32_t f;
+    int status, built = 0;
+    const int J = n * n * n;
+    double *r = malloc(sizeof(double) * J), *z = malloc(sizeof(double) * J);
+    double *p = malloc(sizeof(double) * J), *q = malloc(sizeof(double) * J);
+    float *r32 = malloc(sizeof(float) * J), *e32 = malloc(sizeof(float) * J);
+    for (int i = 0; i < J; i++) x[i] = 0.0;
+    if (mg_build(n, rp, ci, v, &m)) { status = OR_BADINPUT; *iters = 0; *relres = NAN; goto done; }
+    mg32_from(&m, &f);
+    built = 1;
+#define PREC(rv, zv)                                                  \
+    do {                                                              \
+        for (int i_ = 0; i_ < J; i_++) r32[i_] = (float)(rv)[i_];     \
+        vcycle32(&m, &f, 0, r32, e32);                                \
+        for (int i_ = 0; i_ < J; i_++) (zv)[i_] = (double)e32[i_];    \
+    } while (0)
+    for (int i = 0; i < J; i++) r[i] = b[i];
+    PREC(r, z);
+    for (int i = 0; i < J; i++) p[i] = z[i];
+    double bb = dot(J, b, b);
+    double bnorm = sqrt(bb);
+    double rz = dot(J, r, z);
+    double rr = bb;
+    int k = 0;
+    if (!isfinite(bb) || !isfinite(rz)) { status = OR_BADINPUT; *iters = 0; *relres = NAN; goto done; }
+    if (bnorm == 0.0) { status = OR_CONVERGED; *iters = 0; *relres = 0.0; goto done; }
+    status = OR_MAXIT;
+    while (k < maxit) {
+        or_spmv(J, rp, ci, v, p, q);
+        double pq = dot(J, p, q);
+        if (!(pq > 0.0) || !isfinite(pq)) { status = OR_BREAKDOWN; break; }
+        double alpha = rz / pq;
+        for (int i = 0; i < J; i++) {
+            x[i] = x[i] + alpha * p[i];
+            r[i] = r[i] - alpha * q[i];
+        }
+        k++;
+        rr = dot(J, r, r);
+        if (sqrt(rr) <= rtol * bnorm) { status = OR_CONVERGED; break; }
+        PREC(r, z);
+        double rz_new = dot(J, r, z);
+        double beta = rz_new / rz;
+        for (int i = 0; i < J; i++) p[i] = z[i] + beta * p[i];
+        rz = rz_new;
+    }
+#undef PREC
+    *iters = k;
+    *relres = sqrt(rr) / bnorm;
+done:
+    if (built) mg32_free(&m, &f);
+    mg_free(&m);
+    free(r); free(z); free(p); free(q); free(r32); free(e32);
+    return status;
+}

@@ -97,6 +97,13 @@ int    or_mg_apply(int n, const int64_t *rp, const int32_t *ci, const double *v,
 int    or_mgpcg(int n, const int64_t *rp, const int32_t *ci, const double *v, const double *b,
                 double rtol, int maxit, double *x, int *iters, double *relres);
 
+/* The same V-cycle run in float on the hierarchy rounded to float (r rounded
+ * in, z widened out), and CG (in FP64) preconditioned by it. */
+int    or_mg_apply32(int n, const int64_t *rp, const int32_t *ci, const double *v, const double *r,
+                     double *z);
+int    or_mgpcg32(int n, const int64_t *rp, const int32_t *ci, const double *v, const double *b,
+                  double rtol, int maxit, double *x, int *iters, double *relres);
+
 /* ---- pcg.c -------------------------------------------------------------- */
 void or_spmv(int J, const int64_t *rowptr, const int32_t *colidx,
              const double *vals, const double *x, double *y);

@@ -49,12 +49,17 @@ struct MgLevel {
     double *coef = nullptr;                // [E][S][4]: 1/theta, c1, c2, -
     unsigned long long *lmax = nullptr;    // [E][S] bits of the Gershgorin bound
     double *rhs = nullptr, *e = nullptr, *t = nullptr, *d = nullptr, *res = nullptr;
+    // the float copy of the level for the mixed-precision V-cycle (level 0 included)
+    float *vals32 = nullptr, *dinv32 = nullptr, *coef32 = nullptr;
+    float *rhs32 = nullptr, *e32 = nullptr, *t32 = nullptr, *d32 = nullptr, *res32 = nullptr;
 };
 
 struct MgWork {
     int L = 0;
     MgLevel lv[kMgMaxLev];
     double *cinv = nullptr;  // [E][27 * 27][S]: inverse of the coarsest operator
+    float *cinv32 = nullptr;
+    int mixed = 0;           // the V-cycle runs in float on a float copy of the hierarchy
     int *bad = nullptr;      // [E][S]
     // CG state
     double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
@@ -82,7 +87,7 @@ bool mg_levels(int n, int *ns, int *L)
 }
 
 // Lay the workspace out from `base` (nullptr: only count the bytes).
-bool mg_layout(const ens_problem *p, int S, int E, char *base, MgWork *w)
+bool mg_layout(const ens_problem *p, int S, int E, int mixed, char *base, MgWork *w)
 {
     int ns[kMgMaxLev], L;
     if (!mg_levels(p->n, ns, &L)) return false;
@@ -117,6 +122,24 @@ bool mg_layout(const ens_problem *p, int S, int E, char *base, MgWork *w)
         }
     }
     w->cinv = (double *)take(ES * kInv * sizeof(double));
+    w->mixed = mixed;
+    if (mixed) {
+        for (int l = 0; l < L; l++) {
+            MgLevel &v = w->lv[l];
+            const size_t vec = ES * v.J * sizeof(float);
+            v.vals32 = (float *)take(ES * v.nnz * sizeof(float));
+            v.dinv32 = (float *)take(vec);
+            v.coef32 = (float *)take(ES * 4 * sizeof(float));
+            v.rhs32 = (float *)take(vec);
+            v.e32 = (float *)take(vec);
+            if (l < L - 1) {
+                v.t32 = (float *)take(vec);
+                v.d32 = (float *)take(vec);
+                v.res32 = (float *)take(vec);
+            }
+        }
+        w->cinv32 = (float *)take(ES * kInv * sizeof(float));
+    }
     w->bad = (int *)take(ES * sizeof(int));
     const int J = w->lv[0].J;
     const size_t vec0 = ES * J * sizeof(double);
@@ -340,26 +363,30 @@ __global__ void k_mg_chol(int S, const int32_t *__restrict__ rp, const int32_t *
 
 __device__ __forceinline__ bool ens_skip(const int *ens_live, int e) { return ens_live && ens_live[e] == 0; }
 
+// The V-cycle kernels are templates on the value type T of the hierarchy's
+// values, diagonals, coefficients and vectors: double for the FP64 V-cycle,
+// float for the mixed-precision one (CG itself stays in double).
+
 // One row-lane of A x, nonzeros in order.  (Reading the row in chunks of nine,
 // all loads of a chunk issued before its multiply-adds, took 80 registers and
 // three resident blocks per SM instead of eight and made the 31^3 solve 1.6-2x
 // slower, measured: here more warps hide the latency better than more loads
 // in flight per thread.)
-__device__ __forceinline__ double row_dot(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                          const double *__restrict__ v, const double *__restrict__ x, int i,
-                                          int S)
+template <typename T>
+__device__ __forceinline__ T row_dot(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                     const T *__restrict__ v, const T *__restrict__ x, int i, int S)
 {
-    double acc = 0.0;
+    T acc = T(0);
     for (int k = rp[i]; k < rp[i + 1]; k++) acc = fma(v[(size_t)k * S], x[(size_t)ci[k] * S], acc);
     return acc;
 }
 
 // First Chebyshev step: d = D^-1 (b - A x) / theta, x_out = x + d (x = 0 when x_in is null).
+template <typename T>
 __global__ void k_mg_cheb1(int J, int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const double *__restrict__ vals, const double *__restrict__ dinv,
-                           const double *__restrict__ coef, const double *__restrict__ b,
-                           const double *__restrict__ x_in, double *__restrict__ d, double *__restrict__ x_out,
-                           const int *__restrict__ ens_live)
+                           const T *__restrict__ vals, const T *__restrict__ dinv, const T *__restrict__ coef,
+                           const T *__restrict__ b, const T *__restrict__ x_in, T *__restrict__ d,
+                           T *__restrict__ x_out, const int *__restrict__ ens_live)
 {
     int s, i;
     row_lane(S, &s, &i);
@@ -367,22 +394,22 @@ __global__ void k_mg_cheb1(int J, int S, const int32_t *__restrict__ rp, const i
     if (i >= J || ens_skip(ens_live, e)) return;
     const int64_t nnz = rp[J];
     const size_t vb = (size_t)e * J * S + s, o = vb + (size_t)i * S;
-    double x0 = 0.0, res = b[o];
+    T x0 = T(0), res = b[o];
     if (x_in) {
-        res -= row_dot(rp, ci, vals + (size_t)e * nnz * S + s, x_in + vb, i, S);
+        res -= row_dot<T>(rp, ci, vals + (size_t)e * nnz * S + s, x_in + vb, i, S);
         x0 = x_in[o];
     }
-    const double dd = dinv[o] * res * coef[4 * (e * S + s)];
+    const T dd = dinv[o] * res * coef[4 * (e * S + s)];
     d[o] = dd;
     x_out[o] = x0 + dd;
 }
 
 // Second Chebyshev step: d = c1 d + c2 D^-1 (b - A x), x_out = x + d.
+template <typename T>
 __global__ void k_mg_cheb2(int J, int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const double *__restrict__ vals, const double *__restrict__ dinv,
-                           const double *__restrict__ coef, const double *__restrict__ b,
-                           const double *__restrict__ x_in, double *__restrict__ d, double *__restrict__ x_out,
-                           const int *__restrict__ ens_live)
+                           const T *__restrict__ vals, const T *__restrict__ dinv, const T *__restrict__ coef,
+                           const T *__restrict__ b, const T *__restrict__ x_in, T *__restrict__ d,
+                           T *__restrict__ x_out, const int *__restrict__ ens_live)
 {
     int s, i;
     row_lane(S, &s, &i);
@@ -390,17 +417,18 @@ __global__ void k_mg_cheb2(int J, int S, const int32_t *__restrict__ rp, const i
     if (i >= J || ens_skip(ens_live, e)) return;
     const int64_t nnz = rp[J];
     const size_t vb = (size_t)e * J * S + s, o = vb + (size_t)i * S;
-    const double res = b[o] - row_dot(rp, ci, vals + (size_t)e * nnz * S + s, x_in + vb, i, S);
-    const double *c = coef + 4 * (e * S + s);
-    const double dd = fma(c[1], d[o], c[2] * (dinv[o] * res));
+    const T res = b[o] - row_dot<T>(rp, ci, vals + (size_t)e * nnz * S + s, x_in + vb, i, S);
+    const T *c = coef + 4 * (e * S + s);
+    const T dd = fma(c[1], d[o], c[2] * (dinv[o] * res));
     d[o] = dd;
     x_out[o] = x_in[o] + dd;
 }
 
 // res = b - A x
+template <typename T>
 __global__ void k_mg_resid(int J, int S, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const double *__restrict__ vals, const double *__restrict__ b,
-                           const double *__restrict__ x, double *__restrict__ res, const int *__restrict__ ens_live)
+                           const T *__restrict__ vals, const T *__restrict__ b, const T *__restrict__ x,
+                           T *__restrict__ res, const int *__restrict__ ens_live)
 {
     int s, i;
     row_lane(S, &s, &i);
@@ -408,11 +436,12 @@ __global__ void k_mg_resid(int J, int S, const int32_t *__restrict__ rp, const i
     if (i >= J || ens_skip(ens_live, e)) return;
     const int64_t nnz = rp[J];
     const size_t vb = (size_t)e * J * S + s, o = vb + (size_t)i * S;
-    res[o] = b[o] - row_dot(rp, ci, vals + (size_t)e * nnz * S + s, x + vb, i, S);
+    res[o] = b[o] - row_dot<T>(rp, ci, vals + (size_t)e * nnz * S + s, x + vb, i, S);
 }
 
 // rc = P^T rf: the 27 fine nodes of each coarse node, ascending.
-__global__ void k_mg_restrict(int nf, int nc, int S, const double *__restrict__ rf, double *__restrict__ rc,
+template <typename T>
+__global__ void k_mg_restrict(int nf, int nc, int S, const T *__restrict__ rf, T *__restrict__ rc,
                               const int *__restrict__ ens_live)
 {
     int s, I;
@@ -421,19 +450,20 @@ __global__ void k_mg_restrict(int nf, int nc, int S, const double *__restrict__ 
     const int Jc = nc * nc * nc, Jf = nf * nf * nf;
     if (I >= Jc || ens_skip(ens_live, e)) return;
     const int I0 = I % nc, I1 = (I / nc) % nc, I2 = I / (nc * nc);
-    const double *r = rf + (size_t)e * Jf * S + s;
-    double acc = 0.0;
+    const T *r = rf + (size_t)e * Jf * S + s;
+    T acc = T(0);
     for (int i2 = 2 * I2; i2 <= 2 * I2 + 2; i2++)
         for (int i1 = 2 * I1; i1 <= 2 * I1 + 2; i1++)
             for (int i0 = 2 * I0; i0 <= 2 * I0 + 2; i0++) {
-                const double w = w1(i0, I0) * w1(i1, I1) * w1(i2, I2);
+                const T w = (T)(w1(i0, I0) * w1(i1, I1) * w1(i2, I2));
                 acc = fma(w, r[(size_t)(i0 + nf * (i1 + nf * i2)) * S], acc);
             }
     rc[((size_t)e * Jc + I) * S + s] = acc;
 }
 
 // ef += P ec: the (up to 8) coarse parents of each fine node, ascending.
-__global__ void k_mg_prolong_add(int nf, int nc, int S, const double *__restrict__ ec, double *__restrict__ ef,
+template <typename T>
+__global__ void k_mg_prolong_add(int nf, int nc, int S, const T *__restrict__ ec, T *__restrict__ ef,
                                  const int *__restrict__ ens_live)
 {
     int s, i;
@@ -445,30 +475,44 @@ __global__ void k_mg_prolong_add(int nf, int nc, int S, const double *__restrict
     int c0[2], c1[2], c2[2];
     double u0[2], u1[2], u2[2];
     const int m0 = parents(f0, nc, c0, u0), m1 = parents(f1, nc, c1, u1), m2 = parents(f2, nc, c2, u2);
-    const double *c = ec + (size_t)e * Jc * S + s;
-    double acc = 0.0;
+    const T *c = ec + (size_t)e * Jc * S + s;
+    T acc = T(0);
     for (int b2 = 0; b2 < m2; b2++)
         for (int b1 = 0; b1 < m1; b1++)
             for (int b0 = 0; b0 < m0; b0++)
-                acc = fma(u0[b0] * u1[b1] * u2[b2], c[(size_t)(c0[b0] + nc * (c1[b1] + nc * c2[b2])) * S], acc);
+                acc = fma((T)(u0[b0] * u1[b1] * u2[b2]), c[(size_t)(c0[b0] + nc * (c1[b1] + nc * c2[b2])) * S], acc);
     const size_t o = ((size_t)e * Jf + i) * S + s;
     ef[o] = ef[o] + acc;
 }
 
 // Coarsest level: e = A^-1 r, one row-lane per thread (27 products, ascending).
-__global__ void k_mg_coarse_solve(int S, const double *__restrict__ cinv, const double *__restrict__ r,
-                                  double *__restrict__ x, const int *__restrict__ ens_live)
+template <typename T>
+__global__ void k_mg_coarse_solve(int S, const T *__restrict__ cinv, const T *__restrict__ r, T *__restrict__ x,
+                                  const int *__restrict__ ens_live)
 {
     int s, i;
     row_lane(S, &s, &i);
     const int e = blockIdx.y;
     if (i >= kCoarseJ || ens_skip(ens_live, e)) return;
-    const double *a = cinv + ((size_t)e * kInv + i * kCoarseJ) * S + s;
-    const double *rv = r + (size_t)e * kCoarseJ * S + s;
-    double acc = 0.0;
+    const T *a = cinv + ((size_t)e * kInv + i * kCoarseJ) * S + s;
+    const T *rv = r + (size_t)e * kCoarseJ * S + s;
+    T acc = T(0);
 #pragma unroll
     for (int j = 0; j < kCoarseJ; j++) acc = fma(a[(size_t)j * S], rv[(size_t)j * S], acc);
     x[((size_t)e * kCoarseJ + i) * S + s] = acc;
+}
+
+// Element-wise conversions between the CG's double vectors and the float
+// V-cycle (and of the hierarchy at setup), in ensemble order; skipped
+// ensembles (ens_live[e] == 0, with per_ens elements each) are left alone.
+template <typename A, typename B>
+__global__ void k_mg_convert(size_t n, size_t per_ens, const A *__restrict__ src, B *__restrict__ dst,
+                             const int *__restrict__ ens_live)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        if (ens_live && ens_live[t / per_ens] == 0) continue;
+        dst[t] = (B)src[t];
+    }
 }
 
 // ---- CG kernels: 256-row blocks, per-lane block partial sums ---------------------
@@ -689,8 +733,8 @@ __global__ void k_mgcg_final(CgArgs a, int kind, const double *__restrict__ part
 
 inline dim3 rl_grid(int J, int S, int E) { return dim3((unsigned)((J + kBlock / S - 1) / (kBlock / S)), (unsigned)E); }
 
-int mg_check(ens_ctx *h, const char *who, const ens_problem *p, int S, int E, const void *work, size_t work_bytes,
-             MgWork *w)
+int mg_check(ens_ctx *h, const char *who, const ens_problem *p, int S, int E, int mixed, const void *work,
+             size_t work_bytes, MgWork *w)
 {
     if (!h) return ENS_EINVAL;
     if (!p) return set_error(h, ENS_EINVAL, std::string(who) + ": null problem");
@@ -701,56 +745,93 @@ int mg_check(ens_ctx *h, const char *who, const ens_problem *p, int S, int E, co
     std::string why;
     if (problem_check(p, &J, &nnz, &why)) return set_error(h, ENS_EINVAL, std::string(who) + ": " + why);
     if (!lane_count_ok(S) || E < 0) return set_error(h, ENS_EINVAL, std::string(who) + ": bad S / E");
-    if (!mg_layout(p, S, E, nullptr, w))
+    if (mixed != 0 && mixed != 1) return set_error(h, ENS_EINVAL, std::string(who) + ": mixed must be 0 or 1");
+    if (!mg_layout(p, S, E, mixed, nullptr, w))
         return set_error(h, ENS_EINVAL, std::string(who) + ": n must be 2^k - 1 (k >= 2)");
     if (E > 0 && (!work || work_bytes < w->bytes)) return set_error(h, ENS_EINVAL, std::string(who) + ": workspace too small");
-    mg_layout(p, S, E, (char *)work, w);
+    mg_layout(p, S, E, mixed, (char *)work, w);
     return ENS_OK;
 }
 
-int mg_vcycle(ens_ctx *h, const MgWork &w, const int32_t *rp0, const int32_t *ci0, const double *vals0, int S,
-              int E, const double *rhs0, double *e0, const int *ens_live, cudaStream_t st)
+// The arrays of one level in the V-cycle's precision.
+template <typename T> struct LevelView {
+    const T *vals, *dinv, *coef;
+    T *rhs, *e, *t, *d, *res;
+};
+template <typename T> LevelView<T> level_view(const MgLevel &v);
+template <> LevelView<double> level_view<double>(const MgLevel &v)
+{
+    return {v.vals, v.dinv, v.coef, v.rhs, v.e, v.t, v.d, v.res};
+}
+template <> LevelView<float> level_view<float>(const MgLevel &v)
+{
+    return {v.vals32, v.dinv32, v.coef32, v.rhs32, v.e32, v.t32, v.d32, v.res32};
+}
+inline const double *coarse_inverse(const MgWork &w, double *) { return w.cinv; }
+inline const float *coarse_inverse(const MgWork &w, float *) { return w.cinv32; }
+
+// One V-cycle in precision T: e0 = M rhs0 on level 0 (vals0: level 0's values in T).
+template <typename T>
+int mg_vcycle(ens_ctx *h, const MgWork &w, const int32_t *rp0, const int32_t *ci0, const T *vals0, int S, int E,
+              const T *rhs0, T *e0, const int *ens_live, cudaStream_t st)
 {
     const int L = w.L;
-    auto graph = [&](int l, const int32_t **rp, const int32_t **ci, const double **v) {
-        *rp = l ? w.lv[l].rp : rp0;
-        *ci = l ? w.lv[l].ci : ci0;
-        *v = l ? w.lv[l].vals : vals0;
-    };
     for (int l = 0; l < L - 1; l++) {
         const MgLevel &v = w.lv[l];
-        const int32_t *rp, *ci;
-        const double *vals;
-        graph(l, &rp, &ci, &vals);
-        const double *rhs = l ? v.rhs : rhs0;
-        double *e = l ? v.e : e0;
+        const LevelView<T> a = level_view<T>(v);
+        const int32_t *rp = l ? v.rp : rp0, *ci = l ? v.ci : ci0;
+        const T *vals = l ? a.vals : vals0;
+        const T *rhs = l ? a.rhs : rhs0;
+        T *e = l ? a.e : e0;
         const dim3 g = rl_grid(v.J, S, E);
-        k_mg_cheb1<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, v.dinv, v.coef, rhs, nullptr, v.d, v.t, ens_live);
-        k_mg_cheb2<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, v.dinv, v.coef, rhs, v.t, v.d, e, ens_live);
-        k_mg_resid<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, rhs, e, v.res, ens_live);
-        k_mg_restrict<<<rl_grid(w.lv[l + 1].J, S, E), kBlock, 0, st>>>(v.n, w.lv[l + 1].n, S, v.res, w.lv[l + 1].rhs,
-                                                                      ens_live);
+        k_mg_cheb1<T><<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, a.dinv, a.coef, rhs, nullptr, a.d, a.t, ens_live);
+        k_mg_cheb2<T><<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, a.dinv, a.coef, rhs, a.t, a.d, e, ens_live);
+        k_mg_resid<T><<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, rhs, e, a.res, ens_live);
+        k_mg_restrict<T><<<rl_grid(w.lv[l + 1].J, S, E), kBlock, 0, st>>>(v.n, w.lv[l + 1].n, S, a.res,
+                                                                         level_view<T>(w.lv[l + 1]).rhs, ens_live);
     }
     {
-        const MgLevel &v = w.lv[L - 1];
-        const double *rhs = L > 1 ? v.rhs : rhs0;
-        double *e = L > 1 ? v.e : e0;
-        k_mg_coarse_solve<<<rl_grid(kCoarseJ, S, E), kBlock, 0, st>>>(S, w.cinv, rhs, e, ens_live);
+        const LevelView<T> a = level_view<T>(w.lv[L - 1]);
+        const T *rhs = L > 1 ? a.rhs : rhs0;
+        T *e = L > 1 ? a.e : e0;
+        k_mg_coarse_solve<T><<<rl_grid(kCoarseJ, S, E), kBlock, 0, st>>>(S, coarse_inverse(w, (T *)nullptr), rhs,
+                                                                          e, ens_live);
     }
     for (int l = L - 2; l >= 0; l--) {
         const MgLevel &v = w.lv[l];
-        const int32_t *rp, *ci;
-        const double *vals;
-        graph(l, &rp, &ci, &vals);
-        const double *rhs = l ? v.rhs : rhs0;
-        double *e = l ? v.e : e0;
-        const double *ec = w.lv[l + 1].e;  // l + 1 >= 1: a coarse level's correction
+        const LevelView<T> a = level_view<T>(v);
+        const int32_t *rp = l ? v.rp : rp0, *ci = l ? v.ci : ci0;
+        const T *vals = l ? a.vals : vals0;
+        const T *rhs = l ? a.rhs : rhs0;
+        T *e = l ? a.e : e0;
+        const T *ec = level_view<T>(w.lv[l + 1]).e;  // l + 1 >= 1: a coarse level's correction
         const dim3 g = rl_grid(v.J, S, E);
-        k_mg_prolong_add<<<g, kBlock, 0, st>>>(v.n, w.lv[l + 1].n, S, ec, e, ens_live);
-        k_mg_cheb1<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, v.dinv, v.coef, rhs, e, v.d, v.t, ens_live);
-        k_mg_cheb2<<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, v.dinv, v.coef, rhs, v.t, v.d, e, ens_live);
+        k_mg_prolong_add<T><<<g, kBlock, 0, st>>>(v.n, w.lv[l + 1].n, S, ec, e, ens_live);
+        k_mg_cheb1<T><<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, a.dinv, a.coef, rhs, e, a.d, a.t, ens_live);
+        k_mg_cheb2<T><<<g, kBlock, 0, st>>>(v.J, S, rp, ci, vals, a.dinv, a.coef, rhs, a.t, a.d, e, ens_live);
     }
     ENS_LAUNCH_CHECK(h, "multigrid V-cycle");
+    return ENS_OK;
+}
+
+inline unsigned convert_blocks(size_t n)
+{
+    const size_t b = (n + kBlock - 1) / kBlock;
+    return (unsigned)(b < 152 * 16 ? (b ? b : 1) : 152 * 16);
+}
+
+// z = M r with the work's V-cycle: in double, or r rounded to float, the float
+// V-cycle, and its result widened to double.
+int mg_precond(ens_ctx *h, const MgWork &w, const int32_t *rp0, const int32_t *ci0, const double *vals0, int S,
+               int E, const double *r, double *z, const int *ens_live, cudaStream_t st)
+{
+    if (!w.mixed) return mg_vcycle<double>(h, w, rp0, ci0, vals0, S, E, r, z, ens_live, st);
+    const size_t per = (size_t)w.lv[0].J * S, n = per * E;
+    k_mg_convert<double, float><<<convert_blocks(n), kBlock, 0, st>>>(n, per, r, w.lv[0].rhs32, ens_live);
+    const int rc = mg_vcycle<float>(h, w, rp0, ci0, w.lv[0].vals32, S, E, w.lv[0].rhs32, w.lv[0].e32, ens_live, st);
+    if (rc) return rc;
+    k_mg_convert<float, double><<<convert_blocks(n), kBlock, 0, st>>>(n, per, w.lv[0].e32, z, ens_live);
+    ENS_LAUNCH_CHECK(h, "multigrid V-cycle (float)");
     return ENS_OK;
 }
 
@@ -759,23 +840,24 @@ int mg_vcycle(ens_ctx *h, const MgWork &w, const int32_t *rp0, const int32_t *ci
 
 using namespace ens;
 
-extern "C" size_t ens_mg_workspace_size(const ens_problem *p, int S, int E)
+extern "C" size_t ens_mg_workspace_size(const ens_problem *p, int S, int E, int mixed)
 {
     if (!p || (p->kind != ENS_Q1_3D_KL && p->kind != ENS_Q1_3D_DISC) || !lane_count_ok(S) || E < 0) return 0;
+    if (mixed != 0 && mixed != 1) return 0;
     int J;
     int64_t nnz;
     std::string why;
     if (problem_check(p, &J, &nnz, &why)) return 0;
     MgWork w;
-    if (!mg_layout(p, S, E, nullptr, &w)) return 0;
+    if (!mg_layout(p, S, E, mixed, nullptr, &w)) return 0;
     return w.bytes;
 }
 
-extern "C" int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+extern "C" int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, int mixed, const int32_t *rowptr,
                             const int32_t *colidx, const double *vals, void *work, size_t work_bytes, void *stream)
 {
     MgWork w;
-    int rc = mg_check(h, "ens_mg_setup", p, S, E, work, work_bytes, &w);
+    int rc = mg_check(h, "ens_mg_setup", p, S, E, mixed, work, work_bytes, &w);
     if (rc) return rc;
     if (E == 0) return ENS_OK;
     if (!rowptr || !colidx || !vals) return set_error(h, ENS_EINVAL, "ens_mg_setup: null pointer");
@@ -806,15 +888,27 @@ extern "C" int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, co
         k_mg_chol<<<dim3((unsigned)S, (unsigned)E), 32, 0, st>>>(S, w.L > 1 ? c.rp : rowptr, w.L > 1 ? c.ci : colidx,
                                                                   w.L > 1 ? c.vals : vals, w.cinv, w.bad);
     }
+    if (mixed) {  // the float copy of the whole hierarchy, each value rounded once
+        auto cvt = [&](const double *src, float *dst, size_t n) {
+            k_mg_convert<double, float><<<convert_blocks(n), kBlock, 0, st>>>(n, n, src, dst, nullptr);
+        };
+        for (int l = 0; l < w.L; l++) {
+            MgLevel &v = w.lv[l];
+            cvt(l ? v.vals : vals, v.vals32, (size_t)ES * v.nnz);
+            cvt(v.dinv, v.dinv32, (size_t)ES * v.J);
+            cvt(v.coef, v.coef32, (size_t)ES * 4);
+        }
+        cvt(w.cinv, w.cinv32, (size_t)ES * kInv);
+    }
     ENS_LAUNCH_CHECK(h, "ens_mg_setup");
     return ENS_OK;
 }
 
-extern "C" int ens_mg_level(ens_handle h, const ens_problem *p, int S, int E, int level, double *vals_out,
-                            double *lmax_out, const void *work, size_t work_bytes, void *stream)
+extern "C" int ens_mg_level(ens_handle h, const ens_problem *p, int S, int E, int mixed, int level,
+                            double *vals_out, double *lmax_out, const void *work, size_t work_bytes, void *stream)
 {
     MgWork w;
-    int rc = mg_check(h, "ens_mg_level", p, S, E, work, work_bytes, &w);
+    int rc = mg_check(h, "ens_mg_level", p, S, E, mixed, work, work_bytes, &w);
     if (rc) return rc;
     if (level < 0 || level >= w.L) return set_error(h, ENS_EINVAL, "ens_mg_level: no such level");
     if (E == 0) return ENS_OK;
@@ -828,25 +922,25 @@ extern "C" int ens_mg_level(ens_handle h, const ens_problem *p, int S, int E, in
     return ENS_OK;
 }
 
-extern "C" int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+extern "C" int ens_mg_apply(ens_handle h, const ens_problem *p, int S, int E, int mixed, const int32_t *rowptr,
                             const int32_t *colidx, const double *vals, const double *r, double *z, void *work,
                             size_t work_bytes, void *stream)
 {
     MgWork w;
-    int rc = mg_check(h, "ens_mg_apply", p, S, E, work, work_bytes, &w);
+    int rc = mg_check(h, "ens_mg_apply", p, S, E, mixed, work, work_bytes, &w);
     if (rc) return rc;
     if (E == 0) return ENS_OK;
     if (!rowptr || !colidx || !vals || !r || !z) return set_error(h, ENS_EINVAL, "ens_mg_apply: null pointer");
-    return mg_vcycle(h, w, rowptr, colidx, vals, S, E, r, z, nullptr, (cudaStream_t)stream);
+    return mg_precond(h, w, rowptr, colidx, vals, S, E, r, z, nullptr, (cudaStream_t)stream);
 }
 
-extern "C" int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E, const int32_t *rowptr,
+extern "C" int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E, int mixed, const int32_t *rowptr,
                                const int32_t *colidx, const double *vals, const double *b, double *x,
                                const uint8_t *active, double rtol, int maxit, int32_t *iters, double *relres,
                                int32_t *status, void *work, size_t work_bytes, void *stream)
 {
     MgWork w;
-    int rc = mg_check(h, "ens_mgpcg_solve", p, S, E, work, work_bytes, &w);
+    int rc = mg_check(h, "ens_mgpcg_solve", p, S, E, mixed, work, work_bytes, &w);
     if (rc) return rc;
     if (E == 0) return ENS_OK;
     if (!rowptr || !colidx || !vals || !b || !x || !iters || !relres || !status)
@@ -861,7 +955,7 @@ extern "C" int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E,
     ENS_CUDA_CHECK(h, cudaMemsetAsync(w.live_total, 0, sizeof(int), st));
     // x = 0, r = b, z = M r, p = z; b^T b and r^T z decide each lane's start
     k_mgcg_init<<<gred, kBlock, 0, st>>>(J, S, w.nblk, b, x, w.r, w.part0);
-    rc = mg_vcycle(h, w, rowptr, colidx, vals, S, E, w.r, w.z, nullptr, st);
+    rc = mg_precond(h, w, rowptr, colidx, vals, S, E, w.r, w.z, nullptr, st);
     if (rc) return rc;
     k_mgcg_dot<<<gred, kBlock, 0, st>>>(J, S, w.nblk, w.r, w.z, nullptr, nullptr, w.part1);
     k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_INIT, w.part0, w.part1, w);
@@ -882,7 +976,7 @@ extern "C" int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E,
             k_mgcg_update<<<gred, kBlock, 0, st>>>(J, S, w.nblk, x, w.r, w.p, w.q, w.alpha, w.live, w.ens_live,
                                                    w.part0);
             k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_CONV, w.part0, nullptr, w);
-            rc = mg_vcycle(h, w, rowptr, colidx, vals, S, E, w.r, w.z, w.ens_live, st);
+            rc = mg_precond(h, w, rowptr, colidx, vals, S, E, w.r, w.z, w.ens_live, st);
             if (rc) return rc;
             k_mgcg_dot<<<gred, kBlock, 0, st>>>(J, S, w.nblk, w.r, w.z, w.live, w.ens_live, w.part0);
             k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_BETA, w.part0, nullptr, w);

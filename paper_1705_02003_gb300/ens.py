@@ -88,13 +88,15 @@ def _declare(L):
     L.ens_solve_stream.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, vp, vp, vp, c.c_double,
                                    c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
     L.ens_param_indicator.argtypes = [vp, c.POINTER(Problem), c.c_int, vp, vp, vp]
-    L.ens_mg_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
+    L.ens_mg_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int, c.c_int]
     L.ens_mg_workspace_size.restype = c.c_size_t
-    L.ens_mg_setup.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, c.c_size_t, vp]
-    L.ens_mg_level.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, vp, vp, vp, c.c_size_t, vp]
-    L.ens_mg_apply.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, c.c_size_t, vp]
-    L.ens_mgpcg_solve.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, c.c_double,
-                                  c.c_int, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_mg_setup.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_mg_level.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, c.c_int, vp, vp, vp, c.c_size_t,
+                               vp]
+    L.ens_mg_apply.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, c.c_size_t,
+                               vp]
+    L.ens_mgpcg_solve.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp,
+                                  c.c_double, c.c_int, vp, vp, vp, vp, c.c_size_t, vp]
     L.ens_adjoint_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
     L.ens_adjoint_workspace_size.restype = c.c_size_t
     L.ens_adjoint_grad.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
@@ -263,9 +265,10 @@ def ens_spmv(h: Handle, J: int, nnz: int, S: int, E: int, rowptr, colidx, vals, 
     h.check(rc, "ens_spmv")
 
 
-def ens_mg_workspace_size(prob: Problem, S: int, E: int) -> int:
-    """Bytes of workspace of the multigrid calls (0 when the problem has no hierarchy)."""
-    return int(load().ens_mg_workspace_size(ctypes.byref(prob), int(S), int(E)))
+def ens_mg_workspace_size(prob: Problem, S: int, E: int, mixed: bool = False) -> int:
+    """Bytes of workspace of the multigrid calls (0 when the problem has no hierarchy);
+    mixed: the V-cycle runs in float."""
+    return int(load().ens_mg_workspace_size(ctypes.byref(prob), int(S), int(E), int(bool(mixed))))
 
 
 def _mg_sizes(prob, S, E, vals, work):
@@ -278,38 +281,40 @@ def _mg_sizes(prob, S, E, vals, work):
     return J, nnz
 
 
-def ens_mg_setup(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, vals, work, stream=None):
+def ens_mg_setup(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, vals, work, stream=None, mixed=False):
     """Build the per-sample multigrid hierarchy of the fine values into work."""
     _mg_sizes(prob, S, E, vals, work)
-    rc = load().ens_mg_setup(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
-                             _ptr(work), work.numel(), _stream(stream))
+    rc = load().ens_mg_setup(h.ptr, ctypes.byref(prob), int(S), int(E), int(bool(mixed)), _ptr(rowptr),
+                             _ptr(colidx), _ptr(vals), _ptr(work), work.numel(), _stream(stream))
     h.check(rc, "ens_mg_setup")
 
 
-def ens_mg_level(h: Handle, prob: Problem, S: int, E: int, level: int, vals_out, lmax_out, work, stream=None):
+def ens_mg_level(h: Handle, prob: Problem, S: int, E: int, level: int, vals_out, lmax_out, work, stream=None,
+                 mixed=False):
     """Copy a level's Galerkin values [E][nnz_l][S] and Gershgorin bounds [E][S] out of work."""
     for t, nm in ((vals_out, "vals_out"), (lmax_out, "lmax_out")):
         if t is not None:
             _check_dtype(t, torch.float64, nm)
-    rc = load().ens_mg_level(h.ptr, ctypes.byref(prob), int(S), int(E), int(level), _ptr(vals_out), _ptr(lmax_out),
-                             _ptr(work), work.numel(), _stream(stream))
+    rc = load().ens_mg_level(h.ptr, ctypes.byref(prob), int(S), int(E), int(bool(mixed)), int(level),
+                             _ptr(vals_out), _ptr(lmax_out), _ptr(work), work.numel(), _stream(stream))
     h.check(rc, "ens_mg_level")
 
 
-def ens_mg_apply(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, vals, r, z, work, stream=None):
+def ens_mg_apply(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, vals, r, z, work, stream=None,
+                 mixed=False):
     """z = one V-cycle applied to r (hierarchy of the last ens_mg_setup on work)."""
     J, _ = _mg_sizes(prob, S, E, vals, work)
     for t, nm in ((r, "r"), (z, "z")):
         _check_dtype(t, torch.float64, nm)
         if t.numel() != E * J * S:
             raise ValueError(f"{nm} size does not match E, J, S")
-    rc = load().ens_mg_apply(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
-                             _ptr(r), _ptr(z), _ptr(work), work.numel(), _stream(stream))
+    rc = load().ens_mg_apply(h.ptr, ctypes.byref(prob), int(S), int(E), int(bool(mixed)), _ptr(rowptr), _ptr(colidx),
+                             _ptr(vals), _ptr(r), _ptr(z), _ptr(work), work.numel(), _stream(stream))
     h.check(rc, "ens_mg_apply")
 
 
 def ens_mgpcg_solve(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, vals, b, x, active, rtol: float,
-                    maxit: int, iters, relres, status, work, stream=None):
+                    maxit: int, iters, relres, status, work, stream=None, mixed=False):
     """Multigrid-preconditioned ensemble CG (after ens_mg_setup on work)."""
     J, _ = _mg_sizes(prob, S, E, vals, work)
     for t, nm, dt in ((b, "b", torch.float64), (x, "x", torch.float64), (iters, "iters", torch.int32),
@@ -319,9 +324,9 @@ def ens_mgpcg_solve(h: Handle, prob: Problem, S: int, E: int, rowptr, colidx, va
         _check_dtype(active, torch.uint8, "active")
     if b.numel() != E * J * S or x.numel() != E * J * S or iters.numel() != E * S:
         raise ValueError("array sizes do not match E, J, S")
-    rc = load().ens_mgpcg_solve(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(rowptr), _ptr(colidx), _ptr(vals),
-                                _ptr(b), _ptr(x), _ptr(active), float(rtol), int(maxit), _ptr(iters), _ptr(relres),
-                                _ptr(status), _ptr(work), work.numel(), _stream(stream))
+    rc = load().ens_mgpcg_solve(h.ptr, ctypes.byref(prob), int(S), int(E), int(bool(mixed)), _ptr(rowptr),
+                                _ptr(colidx), _ptr(vals), _ptr(b), _ptr(x), _ptr(active), float(rtol), int(maxit),
+                                _ptr(iters), _ptr(relres), _ptr(status), _ptr(work), work.numel(), _stream(stream))
     h.check(rc, "ens_mgpcg_solve")
 
 

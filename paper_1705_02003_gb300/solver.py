@@ -17,12 +17,13 @@ from . import ens
 
 
 class EnsembleSolver:
-    """precond = "jacobi" (ens_pcg_solve) or "mg" (ens_mg_setup + ens_mgpcg_solve:
-    the multigrid V-cycle of the trilinear problems)."""
+    """precond = "jacobi" (ens_pcg_solve), "mg" (ens_mg_setup + ens_mgpcg_solve:
+    the multigrid V-cycle of the trilinear problems) or "mg32" (the same with
+    the V-cycle in float, CG in double)."""
 
     def __init__(self, handle: ens.Handle, prob: ens.Problem, S: int, max_samples: int, rtol: float,
                  maxit: int, device=None, precond: str = "jacobi"):
-        if precond not in ("jacobi", "mg"):
+        if precond not in ("jacobi", "mg", "mg32"):
             raise ValueError(f"unknown preconditioner {precond}")
         self.h = handle
         self.prob = prob
@@ -50,8 +51,9 @@ class EnsembleSolver:
         self.status = torch.empty(lanes, dtype=torch.int32, device=dev)
         self.relres = torch.empty(lanes, **f64)
         self.qoi = torch.empty(lanes, **f64)
-        if precond == "mg":
-            need = ens.ens_mg_workspace_size(prob, self.S, self.Emax)
+        self.mixed = precond == "mg32"
+        if precond != "jacobi":
+            need = ens.ens_mg_workspace_size(prob, self.S, self.Emax, self.mixed)
             if need == 0:
                 raise ValueError("this problem has no multigrid hierarchy (trilinear problems, n = 2^k - 1)")
         else:
@@ -91,10 +93,11 @@ class EnsembleSolver:
         b = self.b[: E * J * S]
         x = self.x[: E * J * S]
         ens.ens_assemble(self.h, self.prob, S, E, self.xi[: L * self.N], self.rowptr, self.colidx, vals, dinv, b)
-        if self.precond == "mg":
-            ens.ens_mg_setup(self.h, self.prob, S, E, self.rowptr, self.colidx, vals, self.work)
+        if self.precond != "jacobi":
+            ens.ens_mg_setup(self.h, self.prob, S, E, self.rowptr, self.colidx, vals, self.work, mixed=self.mixed)
             ens.ens_mgpcg_solve(self.h, self.prob, S, E, self.rowptr, self.colidx, vals, b, x, act, self.rtol,
-                                self.maxit, self.iters[:L], self.relres[:L], self.status[:L], self.work)
+                                self.maxit, self.iters[:L], self.relres[:L], self.status[:L], self.work,
+                                mixed=self.mixed)
         else:
             ens.ens_pcg_solve(self.h, J, nnz, S, E, self.rowptr, self.colidx, vals, dinv, b, x, act, self.rtol,
                               self.maxit, self.iters[:L], self.relres[:L], self.status[:L], self.work)

@@ -65,22 +65,24 @@ class Case:
         E, S = self.E, self.S
         return t.view(E, self.J, S).permute(0, 2, 1).reshape(E * S, self.J).cpu().numpy()
 
-    def mg_work(self):
-        return torch.empty(ens.ens_mg_workspace_size(self.prob, self.S, self.E), dtype=torch.uint8, device="cuda")
+    def mg_work(self, mixed=False):
+        return torch.empty(ens.ens_mg_workspace_size(self.prob, self.S, self.E, mixed), dtype=torch.uint8,
+                           device="cuda")
 
-    def solve_mg(self, rtol, maxit, vals=None, b=None, active=None, work=None):
+    def solve_mg(self, rtol, maxit, vals=None, b=None, active=None, work=None, mixed=False):
         """Multigrid setup + MG-PCG through the C ABI; results per lane as solve()."""
         E, S, J = self.E, self.S, self.J
         dev = "cuda"
         vals = self.vals if vals is None else vals
-        work = self.mg_work() if work is None else work
+        work = self.mg_work(mixed) if work is None else work
         x = torch.full((E * J * S,), float("nan"), dtype=torch.float64, device=dev)
         iters = torch.full((E * S,), -7, dtype=torch.int32, device=dev)
         status = torch.full((E * S,), -7, dtype=torch.int32, device=dev)
         relres = torch.empty(E * S, dtype=torch.float64, device=dev)
-        ens.ens_mg_setup(self.h, self.prob, S, E, self.rowptr, self.colidx, vals, work)
+        ens.ens_mg_setup(self.h, self.prob, S, E, self.rowptr, self.colidx, vals, work, mixed=mixed)
         ens.ens_mgpcg_solve(self.h, self.prob, S, E, self.rowptr, self.colidx, vals, self.b if b is None else b, x,
-                            self.active if active is None else active, rtol, maxit, iters, relres, status, work)
+                            self.active if active is None else active, rtol, maxit, iters, relres, status, work,
+                            mixed=mixed)
         torch.cuda.synchronize()
         xs = x.view(E, J, S).permute(0, 2, 1).reshape(E * S, J).cpu().numpy()
         return dict(x=xs, iters=iters.cpu().numpy(), status=status.cpu().numpy(), relres=relres.cpu().numpy())

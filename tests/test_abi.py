@@ -155,3 +155,4 @@ def test_multigrid_workspace_only_for_the_trilinear_hierarchies():
                 ens.problem("fd7", 31, 6, 3.0), ens.problem("q1", 31, 4, 4.0)):
         assert f(bad, 16, 2) == 0
     assert f(ens.problem("q1_3d_kl", 31, 4, 0.0), 3, 2) == 0  # S must be a power of two
+    assert f(ens.problem("q1_3d_kl", 31, 4, 0.0), 16, 2, mixed=True) > a  # plus the float copy

@@ -195,3 +195,36 @@ def test_mgpcg_status_codes():
     bnan[3] = np.nan
     assert O.mgpcg(n, rp, ci, vals, bnan, 1e-8, 50)[2] == O.BADINPUT
     assert O.mgpcg(n, rp, ci, vals, b, 1e-14, 2)[2] == O.MAXIT
+
+
+@pytest.mark.parametrize("kind", [O.Q1_3D_KL, O.Q1_3D_DISC])
+def test_float_vcycle_is_the_vcycle_to_float_accuracy(kind):
+    """The float V-cycle (hierarchy rounded to float) equals the FP64 V-cycle
+    pinned above to float rounding, and is not the same computation (a dropped
+    term or a wrong coefficient would differ at order one)."""
+    n = 15
+    rp, ci = O.pattern(kind, n)
+    rng = np.random.default_rng(8)
+    for _ in range(2):
+        vals, _ = O.assemble(kind, n, 4, 0.0, rng.uniform(-1, 1, 4), rp, ci)
+        r = rng.standard_normal(n ** 3)
+        z64 = O.mg_apply(n, rp, ci, vals, r)
+        z32 = O.mg_apply32(n, rp, ci, vals, r)
+        rel = np.linalg.norm(z32 - z64) / np.linalg.norm(z64)
+        assert 1e-9 < rel < 1e-6, rel
+
+
+@pytest.mark.parametrize("kind", [O.Q1_3D_KL, O.Q1_3D_DISC])
+def test_cg_with_the_float_vcycle_converges_like_fp64(kind):
+    """CG stays in FP64; the float preconditioner changes neither the count
+    (within one) nor the converged solution (1e-9 at rtol 1e-10)."""
+    n = 15
+    rp, ci = O.pattern(kind, n)
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        vals, b = O.assemble(kind, n, 4, 0.0, rng.uniform(-1, 1, 4), rp, ci)
+        x64, i64, s64, _ = O.mgpcg(n, rp, ci, vals, b, 1e-10, 300)
+        x32, i32, s32, rr = O.mgpcg32(n, rp, ci, vals, b, 1e-10, 300)
+        assert s64 == s32 == O.CONVERGED and rr <= 1e-10
+        assert abs(i32 - i64) <= 1
+        assert np.linalg.norm(x32 - x64) <= 1e-9 * np.linalg.norm(x64)

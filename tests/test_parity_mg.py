@@ -1,8 +1,9 @@
 """GPU parity of the multigrid preconditioner and MG-PCG (csrc/mg.cu) against
 the oracle (oracle/mg.c): the hierarchy's Galerkin operators and Gershgorin
-bounds bit for bit, one V-cycle, the solve on the oracle's matrices and at the
-full 32^3-cell size, status codes, lane independence, and the adaptive loop of
-Section 3.1 run with the multigrid solver."""
+bounds bit for bit, one V-cycle (FP64 and float), the solve on the oracle's
+matrices (FP64 and mixed precision) and at the full 32^3-cell size, status
+codes, lane independence, and the adaptive loop of Section 3.1 run with the
+multigrid solver."""
 import dataclasses
 import os
 
@@ -90,6 +91,32 @@ def test_vcycle_matches_oracle(h, kind):
         assert np.linalg.norm(Z[L] - zo) <= 1e-11 * np.linalg.norm(zo), L
 
 
+@pytest.mark.parametrize("kind", KINDS)
+def test_float_vcycle_matches_oracle(h, kind):
+    """The mixed-precision V-cycle (float copy of the hierarchy, float
+    arithmetic): against the oracle's float V-cycle and its FP64 one, 1e-5 of
+    the result's norm (float rounding ~2e-7 on each side; fused multiply-adds
+    and the coarsest inverse against separate roundings and triangular solves)."""
+    n, S, M = 15, 8, 11
+    c = Case(h, kind, n, 4, 0.0, S, draws(M, 16))
+    rp, ci, V, _, vals, _ = oracle_system(c, kind)
+    rng = np.random.default_rng(6)
+    R = rng.standard_normal((c.E * S, c.J))
+    r = c.upload_lanes(R, c.J)
+    z = torch.empty_like(r)
+    work = c.mg_work(mixed=True)
+    ens.ens_mg_setup(h, c.prob, S, c.E, c.rowptr, c.colidx, vals, work, mixed=True)
+    ens.ens_mg_apply(h, c.prob, S, c.E, c.rowptr, c.colidx, vals, r, z, work, mixed=True)
+    torch.cuda.synchronize()
+    Z = c.lane_vec(z)
+    for L in range(M):
+        z32 = O.mg_apply32(n, rp, ci, V[L], R[L])
+        z64 = O.mg_apply(n, rp, ci, V[L], R[L])
+        assert np.linalg.norm(Z[L] - z32) <= 1e-5 * np.linalg.norm(z32), L
+        assert np.linalg.norm(Z[L] - z64) <= 1e-5 * np.linalg.norm(z64), L
+        assert not np.array_equal(Z[L], z64)  # the float path really ran
+
+
 def _check(got, ref, lanes, bar):
     for j, L in enumerate(lanes):
         assert got["status"][L] == ref[j][2] == O.CONVERGED, L
@@ -111,6 +138,20 @@ def test_mgpcg_matches_oracle_on_the_oracles_matrices(h, kind):
     got = c.solve_mg(1e-7, 500, vals=vals, b=b)
     ref = [O.mgpcg(n, rp, ci, V[L], B[L], 1e-7, 500) for L in range(M)]
     _check(got, ref, range(M), 1e-9)
+    assert all(got["status"][M:] == ens.LANE_INACTIVE)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_mixed_mgpcg_matches_oracle_on_the_oracles_matrices(h, kind):
+    """CG in FP64 with the float V-cycle, on the oracle's matrices and loads:
+    iterations within 1 of the oracle's CG with its float V-cycle, x within 1e-6
+    when the counts agree (the two float preconditioners differ at ~1e-7)."""
+    n, S, M = 15, 16, 21
+    c = Case(h, kind, n, 4, 0.0, S, draws(M, 17))
+    rp, ci, V, B, vals, b = oracle_system(c, kind)
+    got = c.solve_mg(1e-7, 500, vals=vals, b=b, mixed=True)
+    ref = [O.mgpcg32(n, rp, ci, V[L], B[L], 1e-7, 500) for L in range(M)]
+    _check(got, ref, range(M), 1e-6)
     assert all(got["status"][M:] == ens.LANE_INACTIVE)
 
 

@@ -22,7 +22,9 @@
 // The setup (Galerkin products, Gershgorin bounds, Cholesky) follows the order
 // of the textbook sums and rounds each sum on its own (the Galerkin products by
 // the power-of-two weights are exact), so it reproduces a plain host
-// computation bit for bit; the V-cycle itself uses fused multiply-adds.
+// computation bit for bit; the V-cycle itself uses fused multiply-adds.  With
+// `mixed` the hierarchy is also rounded once to float and the V-cycle runs in
+// float (the same kernels instantiated on float); CG stays in double.
 //
 // Layout: every vector of level l is [E][J_l][S] f64, every matrix
 // [E][nnz_l][S] f64 (level 0 is the caller's), the coarsest operator's

@@ -86,6 +86,8 @@ def _declare(L):
     L.or_jacobi.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p]
     L.or_pcg.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_int, _f64p,
                          c.POINTER(c.c_int), c.POINTER(c.c_double)]
+    L.or_pcg_history.argtypes = [c.c_int, _i64p, _i32p, _f64p, _f64p, c.c_double, c.c_int, _f64p,
+                                 c.POINTER(c.c_int), c.POINTER(c.c_double), _f64p]
     L.or_mg_levels.argtypes = [c.c_int, _i32p]
     L.or_mg_galerkin.argtypes = [c.c_int, _i64p, _i32p, _f64p, c.c_int, _i64p, _i32p, _f64p]
     L.or_mg_prolong.argtypes = [c.c_int, c.c_int, _f64p, _f64p]
@@ -224,6 +226,21 @@ def pcg(rowptr, colidx, vals, b, rtol: float, maxit: int):
     st = lib().or_pcg(J, rowptr, colidx, _f64(vals), _f64(b), float(rtol), int(maxit), x,
                       ctypes.byref(it), ctypes.byref(rr))
     return x, it.value, st, rr.value
+
+
+def pcg_history(rowptr, colidx, vals, b, rtol: float, maxit: int):
+    """pcg() that also returns ||r_k|| / ||b|| after every update k = 1..iters
+    (Section 4's per-sample convergence record at every iteration).  With
+    rtol = 0 it runs exactly maxit iterations (barring breakdown).
+    Returns (x, iters, status, relres, history[iters])."""
+    J = len(rowptr) - 1
+    x = np.zeros(J, np.float64)
+    hist = np.zeros(max(1, int(maxit)), np.float64)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().or_pcg_history(J, rowptr, colidx, _f64(vals), _f64(b), float(rtol), int(maxit), x,
+                              ctypes.byref(it), ctypes.byref(rr), hist)
+    return x, it.value, st, rr.value, hist[: it.value].copy()
 
 
 # ---- multigrid V-cycle preconditioner of the trilinear problems (mg.c) ----

@@ -112,6 +112,11 @@ int  or_jacobi(int J, const int64_t *rowptr, const int32_t *colidx,
 int  or_pcg(int J, const int64_t *rowptr, const int32_t *colidx,
             const double *vals, const double *b, double rtol, int maxit,
             double *x, int *iters, double *relres);
+/* or_pcg that also records ||r_k|| / ||b|| after every update k in hist[k - 1]
+ * (hist holds maxit entries; rtol = 0 runs all maxit iterations). */
+int  or_pcg_history(int J, const int64_t *rowptr, const int32_t *colidx,
+                    const double *vals, const double *b, double rtol, int maxit,
+                    double *x, int *iters, double *relres, double *hist);
 /* Assemble + solve M samples, one sample per thread at a time. */
 int  or_solve_batch(int kind, int n, int nparam, double aniso, int M,
                     const double *xi, double rtol, int maxit, int nthreads,

@@ -54,9 +54,12 @@ static double dot(int J, const double *a, const double *b)
     return s;
 }
 
-int or_pcg(int J, const int64_t *rowptr, const int32_t *colidx,
-           const double *vals, const double *b, double rtol, int maxit,
-           double *x, int *iters, double *relres)
+/* The iteration, optionally recording the relative residual ||r_k|| / ||b||
+ * after every update k = 1, 2, ... in hist[k - 1] (Section 4's convergence
+ * record, kept for every iteration instead of only the last). */
+static int pcg_run(int J, const int64_t *rowptr, const int32_t *colidx,
+                   const double *vals, const double *b, double rtol, int maxit,
+                   double *x, int *iters, double *relres, double *hist)
 {
     double *dinv = malloc(sizeof(double) * J), *r = malloc(sizeof(double) * J);
     double *z = malloc(sizeof(double) * J), *p = malloc(sizeof(double) * J);
@@ -90,6 +93,7 @@ int or_pcg(int J, const int64_t *rowptr, const int32_t *colidx,
         }
         k++;
         rr = dot(J, r, r);
+        if (hist) hist[k - 1] = sqrt(rr) / bnorm;
         if (sqrt(rr) <= rtol * bnorm) { status = OR_CONVERGED; break; }
         for (int i = 0; i < J; i++) z[i] = dinv[i] * r[i];
         double rz_new = dot(J, r, z);
@@ -102,6 +106,20 @@ int or_pcg(int J, const int64_t *rowptr, const int32_t *colidx,
 done:
     free(dinv); free(r); free(z); free(p); free(q);
     return status;
+}
+
+int or_pcg(int J, const int64_t *rowptr, const int32_t *colidx,
+           const double *vals, const double *b, double rtol, int maxit,
+           double *x, int *iters, double *relres)
+{
+    return pcg_run(J, rowptr, colidx, vals, b, rtol, maxit, x, iters, relres, NULL);
+}
+
+int or_pcg_history(int J, const int64_t *rowptr, const int32_t *colidx,
+                   const double *vals, const double *b, double rtol, int maxit,
+                   double *x, int *iters, double *relres, double *hist)
+{
+    return pcg_run(J, rowptr, colidx, vals, b, rtol, maxit, x, iters, relres, hist);
 }
 
 /* ---- batch driver: one sample per thread at a time ----------------------- */

@@ -1,8 +1,9 @@
 """Benchmark: sample-solves/s of the surrogate-grouped ensemble PCG.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload q1_256_adaptive] [--no-arms] [--no-layers] [--no-paper] [--no-cpu]
-                    [--mixed-mg]
+                    [--workload q1_256_adaptive] [--no-arms] [--no-cpu]
+                    [--suite layers,configs,c1,pilot,paper,mixed-mg | all]
+                    [--detail-out PATH]
                     [--kernel-only [--kernel-ensembles E]]
 
 A step is one pass of the whole path over the workload: the grid-generation
@@ -12,23 +13,29 @@ level: surrogate grouping (K6, K7), ensemble assembly (K1), ensemble Jacobi-PCG
 sample budget is reached.  value = samples solved / device time (CUDA events
 around K steps, max over ranks).
 
-The same run (one GPU) also reports:
-  arms            parameter-based, natural and random grouping; one sample at a
-                  time on the same GPU; the surrogate groups with lane re-packing
+The LAST line on stdout is one compact JSON object: metric, value, config,
+roofline of the dominant kernel (K2, against the FP64 issue rate measured in
+the same run, with the HBM view beside it), cpu_baseline, e2e, clocks and the
+speed-up over one-sample-at-a-time PCG.  Everything else goes to the detail
+file (--detail-out, default <tmpdir>/ens_bench_detail.json):
+  arms            parameter-based, natural and random grouping; one sample per
+                  call (serial) and all samples of a level in one call at S = 1
+                  (batched); the surrogate groups with lane re-packing -- each
+                  as sample-solves/s and as a fraction of its HBM roofline and
+                  of its path roofline (HBM and FP64)
   R, R_levels     the work ratio of Eq. (R) overall and per level
   level_calls     each level's solve call: size, ensembles, branches, time
-  roofline        the ensemble SpMV (K2) against the FP64 and HBM roofs, and
-                  the whole path against its roofline
-  e2e             the same metric through the public API with host buffers
-  layers          FP32-in-FP64 refinement, batching (two iteration spreads),
-                  the adjoint gradient, each on a bounded sample
-  spmv_configs    K2 on the 7-point 64^3 / 128^3 and 5-point 512^2 problems
-  pilot_grouping  surrogate grouping of a non-adaptive sample set (Section 5)
-  paper_tables    Section 4's Test 1 / Test 2 (32^3 trilinear FEM, N = 4), with
-                  the Jacobi and the multigrid preconditioner: R_l, R,
-                  measured and predicted speed-up for S = 4..32
-                  (--mixed-mg adds the multigrid solve with a float V-cycle)
-  cpu_baseline    the CPU oracle on a bounded sample of the same points
+and, with --suite:
+  layers          FP32-in-FP64 refinement on 1024 draws of 128^3, streamed
+                  batching of all 4096 draws of 64^3, the adjoint gradient of
+                  1024 draws of 512^2, each with per-sample errors against the
+                  oracle on a stated subset
+  configs         K2 on the 7-point 64^3 / 128^3 and 5-point 512^2 problems
+  c1              the 32^2 5-point workload with its four arms
+  pilot           surrogate grouping of a non-adaptive sample set (Section 5)
+  paper           Section 4's Test 1 / Test 2 (32^3 trilinear FEM, N = 4) with
+                  the Jacobi and the multigrid preconditioner
+  mixed-mg        the multigrid solve with a float V-cycle on Test 1 / Test 2
 
 --kernel-only times K2 alone (the case the Nsight Compute summaries use).
 --impl reference times the CPU oracle (the reference arm of this project) on
@@ -43,6 +50,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -54,16 +62,17 @@ if ROOT not in sys.path:
 
 METRIC = "sample-solves/s at rel-res 1e-8: ensemble PCG vs per-sample PCG; SpMV HBM GB/s"
 
+# The FP64 roof from unit counts (context beside the measured one): 152 SMs x
+# 2 FP64 fused multiply-adds per clock x 2.07 GHz.
+FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# FP64 roof of GB300: the FP64 pipe retires two lanes per clock per SM (the
-# pipe-activity counter of K2 gives 1.67 per active cycle at 84 % activity),
-# so 152 SMs x 2 FMA x 2.07 GHz = 630 G FMA/s.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP64_PEAK_SOURCE = "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)"
-
-# DRAM bytes of one K2 launch measured by ncu on the E = 8 case of the same
-# kernel (profiles/k_spmv_q1_256_E8.md), scaled by the units a launch processes.
+# DRAM bytes (read + write) of one K2 launch on the Q1 256^2 problem at S = 16,
+# per ensemble, from an Nsight Compute capture of E = 8 ensembles (0.674 GB
+# read, 0.038 GB written); a full-capacity launch scales it by E.
 SPMV_TRAFFIC_PER_ENSEMBLE = {"q1_256_adaptive": (673.661696e6 + 37.994240e6) / 8}
+
+N_MAX_READING = ("levels of 48, 58 and 159 points; a level that would take the grid past N_max = 512 "
+                 "is not admitted (the fourth would)")
 
 
 def spmv_traffic(wl, E):
@@ -170,6 +179,20 @@ def allmax(pg, v):
     return float(t.item())
 
 
+def timed(stream, fn):
+    """(fn(), seconds) with CUDA events on `stream`, synchronised on both sides."""
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1) / 1e3
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
@@ -188,11 +211,12 @@ def oracle_rate(wl, points: np.ndarray, threads: int):
 
 def oracle_sample_points(wl, count: int):
     """A bounded, deterministic sample of the workload's points: every k-th
-    point of the full sparse grid of the workload's dimension (levels 0..3)."""
-    from paper_1705_02003_gb300 import ens, uq
+    point of the full sparse grid of the workload's dimension (levels 0..3),
+    generated by the oracle's own sparse-grid routines."""
+    import oracle as O
 
-    lvl, idx = ens.ens_sg_initial(wl.nparam, 3)
-    y = uq.coords(lvl, idx)
+    lvl, idx = O.sg_initial(wl.nparam, 3)
+    y = O.sg_points(lvl, idx)
     step = max(1, len(y) // count)
     return y[::step][:count]
 
@@ -225,8 +249,138 @@ def run_reference(args, wl):
 
 
 # ---------------------------------------------------------------------------
+# GPU arm: roofline helpers
+# ---------------------------------------------------------------------------
+def measure_fp64_peak(h, stream, reps: int = 5):
+    """The FP64 fused multiply-add rate of this GPU (TFLOP/s, best of reps),
+    from the throughput kernel ens_fp64_peak on every SM at full occupancy."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens
+
+    blocks, iters = 152 * 8, 4096
+    sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        ens.ens_fp64_peak(h, blocks, iters, sink, stream)
+    best = float("inf")
+    flops = 0.0
+    for _ in range(reps):
+        flops, t = timed(stream, lambda: ens.ens_fp64_peak(h, blocks, iters, sink, stream))
+        best = min(best, t)
+    return flops / best / 1e12
+
+
+def b_alg(nnz: int, J: int, S: int) -> float:
+    """Algorithmic bytes per sample per FP64 Jacobi-PCG iteration: values,
+    nine vector streams (x r/w, r r/w, p r/w, q w+r, D^-1 r) and the graph
+    shared by the S lanes of an ensemble."""
+    return 8 * nnz + 72 * J + (4 * nnz + 4 * (J + 1)) / S
+
+
+def charged_iterations(I: np.ndarray, groups) -> float:
+    """Sample-iterations an ensemble schedule streams: every lane of an
+    ensemble runs until its slowest lane stops.  groups = list of index arrays."""
+    return float(sum(len(g_) and I[g_].max() * len(g_) for g_ in groups))
+
+
+def roof_fracs(value, M, charged, nnz, J, S, hbm_gbs, fp64_tflops):
+    """value as a fraction of the HBM roofline M / (charged B_alg / HBM) and of
+    the path roofline, which also bounds each sample-iteration by its FP64
+    work (nnz + 7 J fused multiply-adds: K2 nnz + J, K3 5 J, K4 J)."""
+    ba = b_alg(nnz, J, S)
+    t_hbm = ba / (hbm_gbs * 1e9)
+    t_fp = 2.0 * (nnz + 7 * J) / (fp64_tflops * 1e12)
+    hbm_roof = M / (charged * t_hbm)
+    path_roof = M / (charged * max(t_hbm, t_fp))
+    return {"hbm_roof": hbm_roof, "hbm_frac": value / hbm_roof, "path_roof": path_roof,
+            "path_frac": value / path_roof, "sample_iterations_charged": charged, "bytes_per_sample_iteration": ba}
+
+
+def level_groups(run, S):
+    """Index arrays of the ensembles of every level of a run (global point indices)."""
+    out = []
+    for (a, b), perm in zip(run["levels"], run["perms"]):
+        perm = np.asarray(perm)
+        for k in range(0, b - a, S):
+            out.append(a + perm[k:k + S])
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def run_arms(h, wl, ad, run, value, stream, hbm, fp64):
+    """The comparison arms of the headline workload, one step each."""
+    from paper_1705_02003_gb300.uq import Adaptive, ratios
+
+    sol = ad.solver
+    M = len(run["I"])
+    J, nnz, S = sol.J, sol.nnz, sol.S
+    arms = {"sur": {"value": value, "R": ratios(run)["run"][1],
+                    **roof_fracs(value, M, charged_iterations(run["I"], level_groups(run, S)), nnz, J, S, hbm, fp64)}}
+    for arm in ("par", "nat", "rand"):
+        r2, ta = timed(stream, lambda: ad.run(arm, seed=0))
+        Ra = ratios(r2)["run"]
+        v = M / ta
+        arms[arm] = {"value": v, "R": Ra[1], "R_levels": Ra[0],
+                     **roof_fracs(v, M, charged_iterations(r2["I"], level_groups(r2, S)), nnz, J, S, hbm, fp64)}
+    # one sample per call (S = 1, E = 1), serially: the same kernels, one solve at a time
+    ps = Adaptive(h, wl, per_sample=True)
+    ps.run("nat")  # warm-up (graph instantiation)
+    r3, tp = timed(stream, lambda: ps.run("nat"))
+    v = M / tp
+    arms["per_sample_serial"] = {
+        "value": v, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r3["I"] - run["I"]))),
+        **roof_fracs(v, M, float(r3["I"].sum()), nnz, J, 1, hbm, fp64)}
+    del ps
+    # one sample per lane, all samples of a level in one call (S = 1, E = M)
+    pb = Adaptive(h, wl, S=1)
+    pb.run("nat")  # warm-up
+    r5, tb = timed(stream, lambda: pb.run("nat"))
+    v = M / tb
+    arms["per_sample_batched"] = {
+        "value": v, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r5["I"] - run["I"]))),
+        "max_iter_diff_vs_serial": int(np.max(np.abs(r5["I"] - r3["I"]))),
+        **roof_fracs(v, M, float(r5["I"].sum()), nnz, J, 1, hbm, fp64)}
+    del pb
+    # the same surrogate groups, each level solved through the batching layer
+    # (live lanes of partly converged ensembles re-packed every 64 trips)
+    rp = Adaptive(h, wl, solver=ad.solver, repack=True)
+    rp.run("sur")  # warm-up
+    r4, tr = timed(stream, lambda: rp.run("sur"))
+    arms["sur_repack"] = {"value": M / tr, "same_grid": bool(np.array_equal(r4["lvl"], run["lvl"])),
+                          "same_iterations": bool(np.array_equal(r4["I"], run["I"]))}
+    del rp
+    for k in ("per_sample_serial", "per_sample_batched"):
+        arms["sur"][f"speedup_vs_{k}"] = value / arms[k]["value"]
+    return arms
+
+
+def spmv_launch(h, sol, E, xi_all, stream, reps=20):
+    """CUDA-event time of one K2 launch (ens_spmv) on E ensembles of the solver's
+    problem, inputs larger than L2."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens
+
+    ens.ens_assemble(h, sol.prob, sol.S, E, xi_all.reshape(-1).contiguous(), sol.rowptr, sol.colidx, sol.vals,
+                     sol.dinv, sol.b)
+    q = torch.empty_like(sol.x)
+    pq = torch.empty(E * sol.S, dtype=torch.float64, device="cuda")
+    call = lambda: ens.ens_spmv(h, sol.J, sol.nnz, sol.S, E, sol.rowptr, sol.colidx, sol.vals, sol.b, q, pq,
+                                sol.work, stream)
+    for _ in range(3):
+        call()
+
+    def many():
+        for _ in range(reps):
+            call()
+
+    _, t = timed(stream, many)
+    del q, pq
+    return t / reps
+
+
 def run_ours(args, wl):
     import torch
 
@@ -236,8 +390,9 @@ def run_ours(args, wl):
     world, rank, local, pg = dist_setup(args)
     if world > 1:
         # N independent replicas: only the timed loop runs on every GPU; the
-        # single-GPU diagnostics (arms, layers, per-problem SpMV) are N = 1 work
-        args.no_arms = args.no_layers = args.no_paper = True
+        # single-GPU diagnostics (arms, suites) are N = 1 work
+        args.no_arms = True
+        args.suite = ""
     torch.cuda.set_device(local)
     h = ens.Handle(local)
     stream = torch.cuda.current_stream()
@@ -266,44 +421,17 @@ def run_ours(args, wl):
     t = ev0.elapsed_time(ev1) / 1e3
     value, tmax = replica_rate(pg, world, M * args.steps, t)
     R = ratios(run)
+    sol = ad.solver
+    hbm, hbm_kind = peaks()
+    fp64 = measure_fp64_peak(h, stream)
 
-    extra = {}
+    detail = {"workload": wl.name, "value": value, "unit": "sample-solves/s",
+              "R": {"sur": R["run"][1], "its": R["its"][1]},
+              "R_levels": {"sur": R["run"][0], "its": R["its"][0], "points": [b - a for a, b in run["levels"]]},
+              "peaks": {"hbm_gbs": hbm, "hbm_source": hbm_kind, "fp64_tflops_measured": fp64,
+                        "fp64_tflops_derived": FP64_DERIVED_TFLOPS}}
     if not args.no_arms:
-        # the other groupings and one-sample-at-a-time PCG, one step each
-        for arm in ("par", "nat", "rand"):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r2 = ad.run(arm, seed=0)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ta = e0.elapsed_time(e1) / 1e3
-            Ra = ratios(r2)["run"]
-            extra[arm] = {"value": M / ta, "R": Ra[1], "R_levels": Ra[0]}
-        ps = Adaptive(h, wl, per_sample=True)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        ps.run("nat")  # warm-up (graph instantiation)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        r3 = ps.run("nat")
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tp = e0.elapsed_time(e1) / 1e3
-        extra["per_sample"] = {"value": M / tp, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r3["I"] - run["I"])))}
-        # the same surrogate groups, each level solved through the batching layer
-        # (live lanes of partly converged ensembles re-packed every 64 trips)
-        rp = Adaptive(h, wl, solver=ad.solver, repack=True)
-        rp.run("sur")  # warm-up
-        torch.cuda.synchronize()
-        e0.record(stream)
-        r4 = rp.run("sur")
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tr = e0.elapsed_time(e1) / 1e3
-        extra["sur_repack"] = {"value": M / tr, "same_grid": bool(np.array_equal(r4["lvl"], run["lvl"])),
-                               "same_iterations": bool(np.array_equal(r4["I"], run["I"]))}
-        del rp
+        detail["arms"] = run_arms(h, wl, ad, run, value, stream, hbm, fp64)
 
     # per solve call (one per level): size, branches and time, from one more step
     ad.time_calls = True
@@ -316,65 +444,34 @@ def run_ours(args, wl):
         charged_c = ad.S * sum(float(it[k:k + ad.S].max()) for k in range(0, M_c, ad.S))
         level_calls.append({"M": M_c, "E": E_c, "branches": ens.ens_pcg_branches(h, E_c),
                             "max_iters": int(it.max()), "ms": ms,
-                            "ps_per_row_lane_iteration": ms * 1e9 / (charged_c * ad.solver.J)})
-
-    layers = {} if args.no_layers else run_layers(h, stream)
-    configs = {} if args.no_layers else run_configs(h, stream)
-    pilot = {} if args.no_layers else run_pilot(h, stream)
-    paper = {} if args.no_paper else run_paper(h, stream)
-    if args.mixed_mg:
-        paper["mixed_multigrid"] = run_mixed_mg(h, stream)
+                            "ps_per_row_lane_iteration": ms * 1e9 / (charged_c * sol.J)})
+    detail["level_calls"] = level_calls
 
     # dominant kernel: the ensemble SpMV (K2) on a full-capacity batch
-    sol = ad.solver
     E = sol.Emax
     L = E * sol.S
-    xi_all = torch.from_numpy(run["y"][:L] if len(run["y"]) >= L else
-                              np.resize(run["y"], (L, wl.nparam))).to("cuda")
-    ens.ens_assemble(h, sol.prob, sol.S, E, xi_all.reshape(-1).contiguous(), sol.rowptr, sol.colidx, sol.vals,
-                     sol.dinv, sol.b)
-    p = sol.b
-    q = torch.empty_like(sol.x)
-    pq = torch.empty(L, dtype=torch.float64, device="cuda")
-    for _ in range(3):
-        ens.ens_spmv(h, sol.J, sol.nnz, sol.S, E, sol.rowptr, sol.colidx, sol.vals, p, q, pq, sol.work)
-    reps = 20
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        ens.ens_spmv(h, sol.J, sol.nnz, sol.S, E, sol.rowptr, sol.colidx, sol.vals, p, q, pq, sol.work)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_spmv = e0.elapsed_time(e1) / 1e3 / reps
+    xi_all = torch.from_numpy(run["y"][:L] if len(run["y"]) >= L else np.resize(run["y"], (L, wl.nparam))).to("cuda")
+    t_spmv = spmv_launch(h, sol, E, xi_all, stream)
     spmv_bytes = E * (8 * sol.nnz * sol.S + 4 * sol.nnz + 4 * (sol.J + 1) + 16 * sol.J * sol.S)
     spmv_fma = E * sol.S * (sol.nnz + sol.J)  # one fused multiply-add per nonzero-lane, one per row-lane for p^T q
-    peak, peak_kind = peaks()
     achieved = spmv_bytes / t_spmv / 1e9
     tflops = 2.0 * spmv_fma / t_spmv / 1e12
-    roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": spmv_traffic(wl, E),
-                "kernel": "k_spmv (K2), FP64", "peak_source": FP64_PEAK_SOURCE,
-                "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "peak_source": peak_kind},
-                "bytes_per_launch": spmv_bytes, "fma_per_launch": spmv_fma, "launch_ms": t_spmv * 1e3}
-    # the whole path: every lane of an ensemble streams until the slowest lane stops
-    charged = sum(float(np.max(run["I"][a + perm[k:k + sol.S]]))
-                  for (a, b), perm in zip(run["levels"], run["perms"]) for k in range(0, b - a, sol.S)) * sol.S
-    b_alg = 8 * sol.nnz + 72 * sol.J + (4 * sol.nnz + 4 * (sol.J + 1)) / sol.S
-    fma_it = sol.nnz + 7 * sol.J  # K2: nnz + J, K3: 5 J (z = D^-1 r stored), K4: J per sample-iteration
-    t_it = max(b_alg / (peak * 1e9), 2.0 * fma_it / (FP64_PEAK_TFLOPS * 1e12))
-    path_roof = M / (charged * t_it)
-    roofline["path"] = {"value": path_roof, "unit": "sample-solves/s", "frac": value / path_roof,
-                        "sample_iterations_charged": charged, "bytes_per_sample_iteration": b_alg,
-                        "fma_per_sample_iteration": fma_it}
+    roofline = {"bound": "alu", "achieved": tflops, "peak": fp64, "unit": "TFLOP/s", "frac": tflops / fp64,
+                "traffic": spmv_traffic(wl, E), "kernel": f"k_spmv (K2), FP64, E={E} S={sol.S}",
+                "peak_source": "measured FP64 FMA rate (ens_fp64_peak, this run)",
+                "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "peak_source": hbm_kind}}
+    detail["spmv"] = {"E": E, "bytes_per_launch": spmv_bytes, "fma_per_launch": spmv_fma, "launch_ms": t_spmv * 1e3,
+                      "fp64_frac_of_derived": tflops / FP64_DERIVED_TFLOPS}
+    path = roof_fracs(value, M, charged_iterations(run["I"], level_groups(run, sol.S)), sol.nnz, sol.J, sol.S,
+                      hbm, fp64)
+    detail["path"] = path
 
     # end to end through the public API with host buffers: the loop copies each
     # level's points in and its surpluses out; in addition every solve's
     # solution fields u (all samples) go to pinned host memory, and the
     # per-sample G, I and surpluses come back at the end of the step
-    host_u = torch.empty(max(M, sol.S) * sol.J + sol.Emax * sol.S * sol.J, dtype=torch.float64,
-                         pin_memory=True)
+    host_u = torch.empty(max(M, sol.S) * sol.J + sol.Emax * sol.S * sol.J, dtype=torch.float64, pin_memory=True)
     moved = {"d2h": 0}
     cursor = {"at": 0}
 
@@ -392,7 +489,7 @@ def run_ours(args, wl):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         cursor["at"] = 0
-        r4 = ad.run("sur")
+        ad.run("sur")
         torch.cuda.synchronize()
     te = time.perf_counter() - t0
     ad.sink = None
@@ -409,39 +506,69 @@ def run_ours(args, wl):
         rate, dt, _ = oracle_rate(wl, pts, threads)
         rate1, dt1, _ = oracle_rate(wl, pts[:2], 1)  # the same solver on one core
         cpu = {"value": rate, "unit": "sample-solves/s", "cores": threads, "kind": "oracle",
-               "sample": f"{len(pts)} of the {M} grid points (every {max(1, M // args.cpu_samples)}-th), "
-                         f"FP64 per-sample Jacobi-PCG, one sample per thread, {dt:.1f} s",
-               "single_core_value": rate1, "single_core_sample": f"the first 2 of those points, {dt1:.1f} s"}
+               "sample": f"{len(pts)} of the {M} grid points, one per thread, {dt:.1f} s"}
+        detail["cpu_baseline"] = dict(cpu, single_core_value=rate1,
+                                      single_core_sample=f"the first 2 of those points, {dt1:.1f} s")
 
+    if rank == 0 and args.suite:
+        detail["suites"] = run_suites(h, stream, args.suite, hbm, fp64)
+
+    h.close()
     if rank == 0:
+        detail_path = args.detail_out or os.path.join(tempfile.gettempdir(), "ens_bench_detail.json")
+        try:
+            os.makedirs(os.path.dirname(os.path.abspath(detail_path)), exist_ok=True)
+            with open(detail_path, "w") as fh:
+                json.dump(detail, fh, indent=1, default=float)
+        except OSError as e:
+            detail_path = f"not written ({e})"
+        arms = detail.get("arms", {})
         line = {
             "metric": METRIC, "value": value, "unit": "sample-solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "kind": wl.kind, "n": wl.n, "J": sol.J, "nnz": sol.nnz,
-                       "N": wl.nparam, "S": sol.S, "samples_per_step": M, "levels": len(run["levels"]),
+            "config": {"workload": wl.name, "problem": "Q1 9-point FEM 256x256, N=4, rotated anisotropy",
+                       "J": sol.J, "nnz": sol.nnz, "S": sol.S, "samples_per_step": M,
+                       "levels": len(run["levels"]), "n_max": wl.n_max, "n_max_reading": N_MAX_READING,
                        "rtol": wl.rtol, "grouping": "sur", "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "l2": "inputs larger than L2 (vals of one level >= 225 MB)"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk,
-            "R": {"sur": R["run"][1], "its": R["its"][1]},
-            "R_levels": {"sur": R["run"][0], "its": R["its"][0],
-                         "points": [b - a for a, b in run["levels"]]},
-            "arms": extra,
-            "level_calls": level_calls,
-            "layers": layers,
-            "spmv_configs": configs,
-            "pilot_grouping": pilot,
-            "paper_tables": paper,
+                       "l2": "inputs larger than L2 (each level's values >= 225 MB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+            "path_frac": path["path_frac"],
+            "speedup_vs_per_sample": {k: arms["sur"][f"speedup_vs_{k}"]
+                                      for k in ("per_sample_serial", "per_sample_batched")} if arms else None,
+            "detail": detail_path,
         }
-        if "per_sample" in extra:
-            line["speedup_vs_per_sample"] = value / extra["per_sample"]["value"]
-        print(json.dumps(line))
-    h.close()
+        print(json.dumps(line, separators=(",", ":")))
     return 0
 
 
-def run_configs(h, stream):
+def run_suites(h, stream, suite: str, hbm: float, fp64: float):
+    names = ["layers", "configs", "c1", "pilot", "paper", "mixed-mg"] if suite == "all" else \
+        [s for s in suite.split(",") if s]
+    out = {}
+    for name in names:
+        t0 = time.perf_counter()
+        if name == "layers":
+            out[name] = run_layers(h, stream)
+        elif name == "configs":
+            out[name] = run_configs(h, stream, hbm, fp64)
+        elif name == "c1":
+            out[name] = run_c1(h, stream, hbm, fp64)
+        elif name == "pilot":
+            out[name] = run_pilot(h, stream)
+        elif name == "paper":
+            out[name] = run_paper(h, stream)
+        elif name == "mixed-mg":
+            out[name] = run_mixed_mg(h, stream)
+        else:
+            raise ValueError(f"unknown suite {name}")
+        out[name]["suite_seconds"] = time.perf_counter() - t0
+        sys.stderr.write(f"suite {name}: {out[name]['suite_seconds']:.1f} s\n")
+    return out
+
+
+def run_configs(h, stream, hbm: float, fp64: float):
     """The ensemble SpMV (K2) on the other problem configurations, each with
     inputs larger than L2: algorithmic GB/s and FP64 rate per launch."""
     import torch
@@ -449,7 +576,6 @@ def run_configs(h, stream):
     from paper_1705_02003_gb300 import ens, inputs
     from paper_1705_02003_gb300.solver import EnsembleSolver
 
-    peak, peak_kind = peaks()
     out = {}
     for name, E in (("fd7_64_batch", 4), ("fd7_128_mixed", 1), ("fd5_512_adjoint", 4)):
         wl = inputs.WORKLOADS[name]
@@ -457,30 +583,45 @@ def run_configs(h, stream):
         S = 32
         sol = EnsembleSolver(h, prob, S, E * S, wl.rtol, wl.maxit)
         xi = torch.from_numpy(inputs.draws(E * S, wl.nparam, seed=wl.seed)).cuda()
-        ens.ens_assemble(h, prob, S, E, xi.reshape(-1), sol.rowptr, sol.colidx, sol.vals, sol.dinv, sol.b)
-        q = torch.empty_like(sol.x)
-        pq = torch.empty(E * S, dtype=torch.float64, device="cuda")
-        call = lambda: ens.ens_spmv(h, sol.J, sol.nnz, S, E, sol.rowptr, sol.colidx, sol.vals, sol.b, q, pq,
-                                    sol.work)
-        for _ in range(3):
-            call()
-        reps = 10
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            call()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3 / reps
+        t = spmv_launch(h, sol, E, xi, stream, reps=10)
         byts = E * (8 * sol.nnz * S + 4 * sol.nnz + 4 * (sol.J + 1) + 16 * sol.J * S)
         fma = E * S * (sol.nnz + sol.J)
         out[name] = {"E": E, "S": S, "bytes_per_launch": byts, "launch_ms": t * 1e3,
-                     "hbm_gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / peak,
-                     "fp64_tflops": 2 * fma / t / 1e12, "fp64_frac": 2 * fma / t / 1e12 / FP64_PEAK_TFLOPS}
-        del sol, q
-    out["peaks"] = {"hbm_gbs": peak, "hbm_source": peak_kind, "fp64_tflops": FP64_PEAK_TFLOPS}
+                     "hbm_gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm,
+                     "fp64_tflops": 2 * fma / t / 1e12, "fp64_frac": 2 * fma / t / 1e12 / fp64}
+        del sol
+        torch.cuda.empty_cache()
+    out["peaks"] = {"hbm_gbs": hbm, "fp64_tflops_measured": fp64}
+    return out
+
+
+def run_c1(h, stream, hbm: float, fp64: float):
+    """The 32 x 32 5-point workload (adaptive grid to level 4, S = 8): its four
+    arms (surrogate, natural, random grouping, one sample per call) and R."""
+    from paper_1705_02003_gb300 import inputs
+    from paper_1705_02003_gb300.uq import Adaptive, ratios
+
+    wl = inputs.WORKLOADS["fd5_32_adaptive"]
+    ad = Adaptive(h, wl)
+    ad.run("sur")
+    out = {"workload": wl.name}
+    ref = None
+    for arm in ("sur", "nat", "rand"):
+        ad.run(arm, seed=0)  # warm-up
+        r, t = timed(stream, lambda: ad.run(arm, seed=0))
+        ref = r if ref is None else ref
+        M = len(r["I"])
+        out[arm] = {"value": M / t, "R": ratios(r)["run"][1],
+                    **roof_fracs(M / t, M, charged_iterations(r["I"], level_groups(r, wl.S)), ad.solver.nnz,
+                                 ad.solver.J, wl.S, hbm, fp64)}
+    ps = Adaptive(h, wl, per_sample=True)
+    ps.run("nat")
+    r, t = timed(stream, lambda: ps.run("nat"))
+    M = len(r["I"])
+    out["per_sample_serial"] = {"value": M / t, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r["I"] - ref["I"]))),
+                                **roof_fracs(M / t, M, float(r["I"].sum()), ad.solver.nnz, ad.solver.J, 1, hbm, fp64)}
+    out["points"] = M
+    out["note"] = "working set in L2 (0.5 MB per ensemble): launch- and latency-bound, roofline fractions are HBM's"
     return out
 
 
@@ -498,26 +639,15 @@ def run_pilot(h, stream):
     prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
     S, M = 32, 512
     sol = EnsembleSolver(h, prob, S, M, wl.rtol, wl.maxit)
-
-    def timed(fn):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        r = fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return r, e0.elapsed_time(e1) / 1e3
-
     pg = uq.PilotGrouping(h, sol, level=1)
-    _, t_pilot = timed(pg.build)
+    _, t_pilot = timed(stream, pg.build)
     xi = torch.from_numpy(inputs.draws(wl.samples, wl.nparam, seed=wl.seed)[:M]).cuda()
-    (pred, perm, _), t_group = timed(lambda: pg.group(xi, S))
+    (pred, perm, _), t_group = timed(stream, lambda: pg.group(xi, S))
     order = perm.to(torch.int64)
     sol.solve(xi)  # warm-up (graph instantiation)
-    (it_nat, *_), t_nat = timed(lambda: sol.solve(xi))
+    (it_nat, *_), t_nat = timed(stream, lambda: sol.solve(xi))
     it_nat = it_nat.cpu().numpy().astype(np.float64)
-    (it_sur, *_), t_sur = timed(lambda: sol.solve(xi.index_select(0, order)))
+    (it_sur, *_), t_sur = timed(stream, lambda: sol.solve(xi.index_select(0, order)))
     p = perm.cpu().numpy()
     R = {}
     for s_ in (8, 16, 32, 64):
@@ -612,8 +742,13 @@ def run_mixed_mg(h, stream):
     """The multigrid preconditioner with its V-cycle in float (CG in double)
     against the FP64 V-cycle, on Section 4's Test 1 and Test 2: one full
     adaptive grid each, surrogate grouping, S = 16; solve-call time, R and the
-    iteration counts (the grid is the same: it depends on G only)."""
-    from paper_1705_02003_gb300 import inputs
+    iteration counts (the grid is the same: it depends on G only); and every
+    solution of 64 draws in one call against the FP64 V-cycle's solution of the
+    same draws (max over samples of max_j |x32_j - x64_j| / max_j |x64_j|)."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens, inputs
+    from paper_1705_02003_gb300.solver import EnsembleSolver
     from paper_1705_02003_gb300.uq import Adaptive, ratios
 
     out = {}
@@ -630,142 +765,208 @@ def run_mixed_mg(h, stream):
             del ad
         res["max_iter_diff"] = int(np.max(np.abs(res["mg32"].pop("I") - res["mg"].pop("I"))))
         res["speedup_mg32_vs_mg"] = res["mg"]["solve_ms"] / res["mg32"]["solve_ms"]
+        prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+        xi = torch.from_numpy(inputs.draws(64, wl.nparam, seed=5)).cuda()
+        xs = {}
+        for pc in ("mg", "mg32"):
+            sol = EnsembleSolver(h, prob, 16, 64, wl.rtol, wl.maxit, precond=pc)
+            it, st, _, _ = sol.solve(xi)
+            assert bool((st == ens.LANE_CONVERGED).all().item())
+            xs[pc] = sol.solution(64).permute(0, 2, 1).reshape(64, sol.J).clone()
+            del sol
+        err = ((xs["mg32"] - xs["mg"]).abs().amax(dim=1) / xs["mg"].abs().amax(dim=1)).max().item()
+        res["max_rel_error_vs_fp64_vcycle"] = err
+        res["error_sample"] = "64 draws (seed 5) at rtol 1e-7, one call of 4 ensembles of 16"
         out[name] = res
+        torch.cuda.empty_cache()
     return out
 
 
+def _lanes_to_rows(x, E, J, S):
+    """[E][J][S] device vector -> [E*S][J]."""
+    return x[: E * J * S].view(E, J, S).permute(0, 2, 1).reshape(E * S, J)
+
+
 def run_layers(h, stream):
-    """The three system layers on bounded samples of their workloads:
-    FP32-in-FP64 refinement vs the FP64 solve on the 128^3 problem (one
-    ensemble), continuous batching with an autotuned S vs fixed batches on the
-    64^3 problem, the adjoint gradient on the 512^2 problem (one ensemble)."""
+    """The three system layers at their configurations' sizes, each with
+    per-sample results against the oracle on a stated subset (timed on all
+    host cores):
+      precision       1024 draws of the 128^3 7-point problem, S = 32, FP32
+                      values and inner Jacobi-PCG inside FP64 refinement to
+                      1e-10, in calls of 8 ensembles, against the FP64 solve;
+      batching        all 4096 draws of the 64^3 problem through a pool of 1024
+                      lanes, S autotuned over {8, 16, 32, 64}, against fixed
+                      batches of 1024 draws;
+      differentiation 1024 draws of the 512^2 5-point problem, S = 32: Q and
+                      dQ/dxi from the forward and adjoint ensemble solves."""
     import torch
 
-    from paper_1705_02003_gb300 import adjoint, ens, inputs
+    import oracle as O
+    from paper_1705_02003_gb300 import adjoint, batching, ens, inputs
     from paper_1705_02003_gb300.solver import EnsembleSolver
 
+    threads = os.cpu_count() or 1
     out = {}
 
-    def timed(fn):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        r = fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return r, e0.elapsed_time(e1) / 1e3
-
-    # precision layer
+    # ---- precision layer --------------------------------------------------
     wl = inputs.WORKLOADS["fd7_128_mixed"]
     prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
-    sol = EnsembleSolver(h, prob, wl.S, wl.S, wl.rtol, wl.maxit)
-    xi = torch.from_numpy(inputs.draws(wl.S, wl.nparam, seed=wl.seed)).cuda()
-    J, nnz, S = sol.J, sol.nnz, sol.S
-    ens.ens_assemble(h, prob, S, 1, xi.reshape(-1), sol.rowptr, sol.colidx, sol.vals, sol.dinv, sol.b)
-    v32 = torch.empty(nnz * S, dtype=torch.float32, device="cuda")
-    ens.ens_assemble(h, prob, S, 1, xi.reshape(-1), sol.rowptr, sol.colidx, v32)
-    x64 = torch.empty(J * S, dtype=torch.float64, device="cuda")
-    it64 = torch.empty(S, dtype=torch.int32, device="cuda")
-    st64 = torch.empty_like(it64)
-    rr64 = torch.empty(S, dtype=torch.float64, device="cuda")
-    _, t64 = timed(lambda: ens.ens_pcg_solve(h, J, nnz, S, 1, sol.rowptr, sol.colidx, sol.vals, sol.dinv, sol.b,
-                                             x64, None, wl.rtol, wl.maxit, it64, rr64, st64, sol.work))
-    xir = torch.empty(J * S, dtype=torch.float64, device="cuda")
-    itir = torch.empty(S, dtype=torch.int32, device="cuda")
-    oit = torch.empty_like(itir)
-    stir = torch.empty_like(itir)
-    rrir = torch.empty(S, dtype=torch.float64, device="cuda")
-    wir = torch.empty(ens.ens_pcg_ir_workspace_size(J, nnz, S, 1), dtype=torch.uint8, device="cuda")
-    # the inner tolerance trades FP32 iterations per correction against corrections:
-    # time each candidate once and keep the fastest (the last run's results are reported)
-    tune = {}
-    for tin in (1e-3, 1e-4, 1e-5, 1e-6):
-        _, tt = timed(lambda: ens.ens_pcg_solve_ir(h, J, nnz, S, 1, sol.rowptr, sol.colidx, sol.vals, v32,
-                                                   sol.dinv, sol.b, xir, None, wl.rtol, tin, wl.maxit, 50, itir,
-                                                   oit, rrir, stir, wir))
-        tune[tin] = tt
+    S, M, Ec = wl.S, wl.samples, 8
+    xi_all = inputs.draws(M, wl.nparam, seed=wl.seed)
+    sub = np.arange(0, M, M // 16)  # 16 samples checked against the oracle
+    sol = EnsembleSolver(h, prob, S, Ec * S, wl.rtol, wl.maxit)
+    J, nnz = sol.J, sol.nnz
+    v32 = torch.empty(Ec * nnz * S, dtype=torch.float32, device="cuda")
+    xir = torch.empty(Ec * J * S, dtype=torch.float64, device="cuda")
+    L = Ec * S
+    itir = torch.empty(L, dtype=torch.int32, device="cuda")
+    oit, stir = torch.empty_like(itir), torch.empty_like(itir)
+    rrir = torch.empty(L, dtype=torch.float64, device="cuda")
+    wir = torch.empty(ens.ens_pcg_ir_workspace_size(J, nnz, S, Ec), dtype=torch.uint8, device="cuda")
+
+    def assemble(c0, E):
+        xi = torch.from_numpy(xi_all[c0:c0 + E * S]).cuda()
+        ens.ens_assemble(h, prob, S, E, xi.reshape(-1), sol.rowptr, sol.colidx, sol.vals[: E * nnz * S],
+                         sol.dinv[: E * J * S], sol.b[: E * J * S])
+        ens.ens_assemble(h, prob, S, E, xi.reshape(-1), sol.rowptr, sol.colidx, v32[: E * nnz * S])
+
+    def ir(E, tin):
+        ens.ens_pcg_solve_ir(h, J, nnz, S, E, sol.rowptr, sol.colidx, sol.vals[: E * nnz * S], v32[: E * nnz * S],
+                             sol.dinv[: E * J * S], sol.b[: E * J * S], xir[: E * J * S], None, wl.rtol, tin,
+                             wl.maxit, 50, itir[: E * S], oit[: E * S], rrir[: E * S], stir[: E * S], wir)
+
+    def fp64(E):
+        ens.ens_pcg_solve(h, J, nnz, S, E, sol.rowptr, sol.colidx, sol.vals[: E * nnz * S], sol.dinv[: E * J * S],
+                          sol.b[: E * J * S], sol.x[: E * J * S], None, wl.rtol, wl.maxit, sol.iters[: E * S],
+                          sol.relres[: E * S], sol.status[: E * S], sol.work)
+
+    # the inner tolerance trades FP32 iterations per correction against
+    # corrections: time each candidate on the first ensemble, keep the fastest
+    assemble(0, 1)
+    tune = {tin: timed(stream, lambda: ir(1, tin))[1] for tin in (1e-3, 1e-4, 1e-5, 1e-6)}
     best = min(tune, key=tune.get)
-    _, tir = timed(lambda: ens.ens_pcg_solve_ir(h, J, nnz, S, 1, sol.rowptr, sol.colidx, sol.vals, v32, sol.dinv,
-                                                sol.b, xir, None, wl.rtol, best, wl.maxit, 50, itir, oit, rrir,
-                                                stir, wir))
-    d = (xir - x64).view(J, S)
-    err = (d.norm(dim=0) / x64.view(J, S).norm(dim=0)).max().item()
-    out["precision"] = {
-        "workload": wl.name, "sample": f"one ensemble of {S} draws",
-        "fp64_value": S / t64, "ir_value": S / tir, "unit": "sample-solves/s", "speedup": t64 / tir,
-        "fp64_max_iters": int(it64.max().item()), "ir_inner_iters_max": int(itir.max().item()),
-        "ir_outer_max": int(oit.max().item()), "max_relres": float(rrir.max().item()),
-        "max_rel_error_vs_fp64": err, "rtol_inner": best,
-        "rtol_inner_seconds": {f"{k:g}": v for k, v in tune.items()},
-        "all_converged": bool((stir == 0).all().item() and (st64 == 0).all().item())}
-    del sol, v32, wir, x64, xir
+    t64 = tir = 0.0
+    its64, itsir, outer, relres, conv = [], [], [], [], True
+    err_fp64, gpu_sub = [], {}
+    for c0 in range(0, M, Ec * S):
+        assemble(c0, Ec)
+        _, t = timed(stream, lambda: fp64(Ec))
+        t64 += t
+        _, t = timed(stream, lambda: ir(Ec, best))
+        tir += t
+        conv &= bool((stir == 0).all().item() and (sol.status[:L] == 0).all().item())
+        its64.append(sol.iters[:L].cpu().numpy())
+        itsir.append(itir.cpu().numpy())
+        outer.append(oit.cpu().numpy())
+        relres.append(rrir.cpu().numpy())
+        x64r = _lanes_to_rows(sol.x, Ec, J, S)
+        xirr = _lanes_to_rows(xir, Ec, J, S)
+        err_fp64.append(((xirr - x64r).abs().amax(dim=1) / x64r.abs().amax(dim=1)).cpu().numpy())
+        for m in sub[(sub >= c0) & (sub < c0 + L)]:
+            gpu_sub[int(m)] = (xirr[m - c0].cpu().numpy(), x64r[m - c0].cpu().numpy(), int(sol.iters[m - c0].item()))
+    del sol, v32, wir, xir
     torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    ref = O.solve_batch(O.FD7_AXIS, wl.n, wl.nparam, wl.aniso, xi_all[sub], wl.rtol, wl.maxit, nthreads=threads,
+                        want_x=True)
+    t_or = time.perf_counter() - t0
+    e_ir = [np.abs(gpu_sub[int(m)][0] - ref["x"][k]).max() / np.abs(ref["x"][k]).max() for k, m in enumerate(sub)]
+    e_64 = [np.abs(gpu_sub[int(m)][1] - ref["x"][k]).max() / np.abs(ref["x"][k]).max() for k, m in enumerate(sub)]
+    d_it = [gpu_sub[int(m)][2] - int(ref["iters"][k]) for k, m in enumerate(sub)]
+    out["precision"] = {
+        "workload": wl.name, "samples": M, "S": S, "ensembles_per_call": Ec,
+        "fp64_value": M / t64, "ir_value": M / tir, "unit": "sample-solves/s", "speedup": t64 / tir,
+        "rtol_inner": best, "rtol_inner_seconds_one_ensemble": {f"{k:g}": v for k, v in tune.items()},
+        "fp64_iters_min_max": [int(np.min(its64)), int(np.max(its64))],
+        "ir_inner_iters_max": int(np.max(itsir)), "ir_outer_max": int(np.max(outer)),
+        "max_relres_fp64_residual": float(np.max(relres)), "all_converged": conv,
+        "max_rel_error_ir_vs_fp64_gpu_all_samples": float(np.max(err_fp64)),
+        "oracle_subset": f"{len(sub)} samples (every {M // len(sub)}th), FP64 oracle, {threads} threads, {t_or:.0f} s",
+        "max_rel_error_ir_vs_oracle": float(np.max(e_ir)), "max_rel_error_fp64_vs_oracle": float(np.max(e_64)),
+        "fp64_iter_diff_vs_oracle": d_it, "error_norm": "max_j |x_j - x_oracle_j| / max_j |x_oracle_j|"}
 
-    # batching layer: the same samples through a fixed lane capacity, as fixed
-    # batches solved to completion one after another vs continuous refill
-    from paper_1705_02003_gb300 import batching
+    # ---- batching layer ---------------------------------------------------
+    wl = inputs.WORKLOADS["fd7_64_batch"]
+    prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    M, lanes = wl.samples, 1024
+    xi_h = inputs.draws(M, wl.nparam, seed=wl.seed)
+    xi = torch.from_numpy(xi_h).cuda()
+    S, tune = batching.autotune(h, prob, xi[:512], lanes=256, rtol=wl.rtol, maxit=wl.maxit, chunk=32, stream=stream)
+    chunk, ctune = batching.autotune_chunk(h, prob, xi[:512], 256, S, wl.rtol, wl.maxit, stream=stream)
+    E = lanes // S
+    work = torch.empty(ens.ens_stream_workspace_size(prob, S, E), dtype=torch.uint8, device="cuda")
+    batching.solve_stream(h, prob, xi[:lanes], S, E, wl.rtol, wl.maxit, chunk=chunk, work=work)  # warm-up
+    res, tstream = timed(stream, lambda: batching.solve_stream(h, prob, xi, S, E, wl.rtol, wl.maxit, chunk=chunk,
+                                                               work=work))
+    del work
+    fsol = EnsembleSolver(h, prob, S, lanes, wl.rtol, wl.maxit)
+    fsol.solve(xi[:lanes])  # warm-up
 
-    def batching_case(name, M, lanes, S=None, order_note="the first"):
-        wl = inputs.WORKLOADS[name]
-        prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
-        total = wl.samples if wl.samples else M
-        xi = torch.from_numpy(inputs.draws(total, wl.nparam, seed=wl.seed)[:M]).cuda()
-        tune, ctune, chunk = {}, {}, 32
-        if S is None:
-            S, tune = batching.autotune(h, prob, xi, lanes=lanes, rtol=wl.rtol, maxit=wl.maxit, chunk=32,
-                                        stream=stream)
-            chunk, ctune = batching.autotune_chunk(h, prob, xi, lanes, S, wl.rtol, wl.maxit, stream=stream)
-        E = lanes // S
-        work = torch.empty(ens.ens_stream_workspace_size(prob, S, E), dtype=torch.uint8, device="cuda")
-        batching.solve_stream(h, prob, xi[:lanes], S, E, wl.rtol, wl.maxit, chunk=chunk, work=work)  # warm-up
-        # the streamed solve syncs with the host every `chunk` trips: best of two runs
-        runs_s = [timed(lambda: batching.solve_stream(h, prob, xi, S, E, wl.rtol, wl.maxit, chunk=chunk,
-                                                      work=work)) for _ in range(2)]
-        res, tstream = min(runs_s, key=lambda rt: rt[1])
-        del work
-        fsol = EnsembleSolver(h, prob, S, lanes, wl.rtol, wl.maxit)
-        fsol.solve(xi[:lanes])  # warm-up
+    def fixed():
+        its, qs = [], []
+        for a0 in range(0, M, lanes):
+            it, _, _, q = fsol.solve(xi[a0:a0 + lanes])
+            its.append(it.clone())
+            qs.append(q.clone())
+        return torch.cat(its), torch.cat(qs)
 
-        def fixed():
-            its = []
-            for a0 in range(0, M, lanes):
-                it, _, _, _ = fsol.solve(xi[a0:a0 + lanes])
-                its.append(it.clone())
-            return torch.cat(its)
+    (fits, fq), tfixed = timed(stream, fixed)
+    del fsol
+    torch.cuda.empty_cache()
+    sub = np.arange(0, M, M // 16)
+    t0 = time.perf_counter()
+    ref = O.solve_batch(O.FD7_AXIS, wl.n, wl.nparam, wl.aniso, xi_h[sub], wl.rtol, wl.maxit, nthreads=threads)
+    t_or = time.perf_counter() - t0
+    it_s = res["iters"].cpu().numpy()
+    q_s = res["qoi"].cpu().numpy()
+    out["batching"] = {
+        "workload": wl.name, "samples": M, "lanes": lanes, "S": S, "S_autotune_seconds": {str(k): v for k, v in tune.items()},
+        "chunk": chunk, "chunk_autotune_seconds": {str(k): v for k, v in ctune.items()},
+        "autotune_sample": "the first 512 draws through 256 lanes",
+        "stream_value": M / tstream, "fixed_batches_value": M / tfixed, "unit": "sample-solves/s",
+        "speedup": tfixed / tstream, "iters_min_max": [int(it_s.min()), int(it_s.max())],
+        "same_iterations_as_fixed": bool(np.array_equal(it_s, fits.cpu().numpy())),
+        "all_converged": bool((res["status"] == 0).all().item()),
+        "oracle_subset": f"{len(sub)} draws (every {M // len(sub)}th), {threads} threads, {t_or:.0f} s",
+        "iter_diff_vs_oracle": (it_s[sub] - ref["iters"]).astype(int).tolist(),
+        "max_G_rel_error_vs_oracle": float(np.max(np.abs(q_s[sub] - ref["G"]) / ref["G"]))}
+    del xi
 
-        runs_f = [timed(fixed) for _ in range(2)]
-        fits, tfixed = min(runs_f, key=lambda rt: rt[1])
-        del fsol
-        torch.cuda.empty_cache()
-        return {"workload": name, "sample": f"{M} uniform draws ({order_note}), {lanes} lanes", "S": S,
-                "S_autotuned": bool(tune), "autotune_seconds": {str(k): v for k, v in tune.items()},
-                "chunk": chunk, "chunk_autotune_seconds": {str(k): v for k, v in ctune.items()},
-                "stream_value": M / tstream, "fixed_batches_value": M / tfixed, "unit": "sample-solves/s",
-                "timing": "best of 2 runs each", "stream_seconds": [t for _, t in runs_s],
-                "fixed_seconds": [t for _, t in runs_f], "speedup": tfixed / tstream,
-                "iters_min_max": [int(res["iters"].min().item()), int(res["iters"].max().item())],
-                "same_iterations_as_fixed": bool(torch.equal(res["iters"], fits))}
-
-    out["batching"] = batching_case("fd7_64_batch", 256, 64, order_note="the first of the 4096")
-    # the same comparison where the counts spread widely (10^(4 xi_1) anisotropy)
-    out["batching_wide_spread"] = batching_case("q1_256_adaptive", 128, 64, S=16, order_note="seed 0")
-
-    # differentiation layer
+    # ---- differentiation layer --------------------------------------------
     wl = inputs.WORKLOADS["fd5_512_adjoint"]
     prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
-    w = torch.from_numpy(inputs.region_weights(wl.n, 2))
-    asol = adjoint.AdjointSolver(h, prob, wl.S, wl.S, w, wl.rtol, wl.maxit)
-    xi = torch.from_numpy(inputs.draws(wl.S, wl.nparam, seed=wl.seed)).cuda()
-    _, tf = timed(lambda: asol.forward(xi))
-    _, tg = timed(lambda: asol.gradient(xi, recompute_forward=False))
-    out["differentiation"] = {
-        "workload": wl.name, "sample": f"one ensemble of {wl.S} draws",
-        "forward_value": wl.S / tf, "gradient_value": wl.S / (tf + tg), "unit": "samples/s (Q and dQ/dxi)",
-        "forward_max_iters": int(asol.last["forward_iters"].max().item()),
-        "adjoint_max_iters": int(asol.last["adjoint_iters"].max().item())}
+    M = wl.samples
+    w_h = inputs.region_weights(wl.n, 2)
+    asol = adjoint.AdjointSolver(h, prob, wl.S, M, torch.from_numpy(w_h), wl.rtol, wl.maxit)
+    xi_h = inputs.draws(M, wl.nparam, seed=wl.seed)
+    xi = torch.from_numpy(xi_h).cuda()
+    asol.forward(xi[: wl.S])  # warm-up
+    Q, tf = timed(stream, lambda: asol.forward(xi))
+    g, tg = timed(stream, lambda: asol.gradient(xi, recompute_forward=False))
+    fit = asol.last["forward_iters"].cpu().numpy()
+    ait = asol.last["adjoint_iters"].cpu().numpy()
+    conv = bool((asol.last["forward_status"] == 0).all().item() and (asol.last["adjoint_status"] == 0).all().item())
+    Qh, gh = Q.cpu().numpy(), g.cpu().numpy()
     del asol
     torch.cuda.empty_cache()
+    sub = np.arange(0, M, M // 16)
+    from concurrent.futures import ThreadPoolExecutor
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        refs = list(ex.map(lambda m: O.adjoint_grad(O.FD5_LOGKL, wl.n, wl.nparam, wl.aniso, xi_h[m], w_h, wl.rtol,
+                                                    wl.maxit), sub))
+    t_or = time.perf_counter() - t0
+    gerr = [np.abs(gh[m] - r[1]).max() / np.abs(r[1]).max() for m, r in zip(sub, refs)]
+    qerr = [abs(Qh[m] - r[0]) / abs(r[0]) for m, r in zip(sub, refs)]
+    out["differentiation"] = {
+        "workload": wl.name, "samples": M, "S": wl.S, "ensembles_per_call": M // wl.S,
+        "forward_value": M / tf, "gradient_value": M / (tf + tg), "unit": "samples/s (Q, and Q with dQ/dxi)",
+        "forward_iters_max": int(fit.max()), "adjoint_iters_max": int(ait.max()), "all_converged": conv,
+        "oracle_subset": f"{len(sub)} draws (every {M // len(sub)}th), oracle adjoint at the same rtol, "
+                         f"{threads} threads, {t_or:.0f} s",
+        "max_rel_error_Q_vs_oracle": float(np.max(qerr)), "max_rel_error_grad_vs_oracle": float(np.max(gerr)),
+        "error_norm": "max_k |g_k - g_oracle_k| / max_k |g_oracle_k| per sample"}
     return out
 
 
@@ -780,7 +981,7 @@ def run_kernel_only(args, wl):
 
     h = ens.Handle(0)
     prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
-    S = wl.S
+    S = args.kernel_s or wl.S
     E = args.kernel_ensembles
     sol = EnsembleSolver(h, prob, S, E * S, wl.rtol, wl.maxit)
     xi = torch.from_numpy(inputs.draws(E * S, wl.nparam, seed=1)).cuda()
@@ -799,9 +1000,11 @@ def run_kernel_only(args, wl):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / args.steps
     byts = E * (8 * sol.nnz * S + 4 * sol.nnz + 4 * (sol.J + 1) + 16 * sol.J * S)
+    fma = E * S * (sol.nnz + sol.J)
     peak, _ = peaks()
     print(json.dumps({"kernel": "k_spmv", "workload": wl.name, "E": E, "S": S, "ms": t * 1e3,
-                      "bytes": byts, "GBps": byts / t / 1e9, "frac": byts / t / 1e9 / peak}))
+                      "bytes": byts, "GBps": byts / t / 1e9, "frac": byts / t / 1e9 / peak,
+                      "fp64_tflops": 2 * fma / t / 1e12}))
     h.close()
     return 0
 
@@ -815,14 +1018,13 @@ def main():
     ap.add_argument("--workload", default="q1_256_adaptive")
     ap.add_argument("--no-arms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-layers", action="store_true")
-    ap.add_argument("--no-paper", action="store_true", help="skip the Section 4 tables (Test 1 / Test 2)")
-    ap.add_argument("--mixed-mg", action="store_true",
-                    help="also time the multigrid solve with its V-cycle in float on Test 1 / Test 2")
+    ap.add_argument("--suite", default="", help="comma-separated: layers, configs, c1, pilot, paper, mixed-mg; or all")
+    ap.add_argument("--detail-out", default=None, help="where to write the detail JSON")
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--ref-samples", type=int, default=32)
     ap.add_argument("--kernel-only", action="store_true", help="time the ensemble SpMV alone (profiling)")
     ap.add_argument("--kernel-ensembles", type=int, default=8)
+    ap.add_argument("--kernel-s", type=int, default=0, help="lanes per ensemble for --kernel-only (0: the workload's)")
     args = ap.parse_args()
     from paper_1705_02003_gb300 import inputs
 

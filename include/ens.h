@@ -188,10 +188,16 @@ int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
 /* Mixed precision (`mixed` = 1; 0 = FP64 throughout): the hierarchy is built
  * in FP64 as described, then rounded once to float, and every V-cycle runs in
  * float (r rounded in, z widened out); CG, its inner products, residual test
- * and iterate stay FP64.  The preconditioner only approximates A^-1, so its
+ * and iterate stay FP64.  Each lane's r is scaled by a power of two that puts
+ * its largest entry in [1, 2) before the rounding and z is scaled back (exact,
+ * and the V-cycle commutes with it), so any lane magnitude FP64 represents
+ * stays inside float's range; entries more than 2^125 below a lane's largest
+ * round to zero.  The preconditioner only approximates A^-1, so its
  * rounding changes the iteration counts little (the FP32 and FP64 V-cycles
  * differ by ~2e-7 relative).  Every call on one workspace uses the same p, S,
- * E and `mixed` (the layout depends on them).
+ * E and `mixed` (the layout depends on them): the handle records them at
+ * ens_mg_setup (for its last 16 workspaces), and ens_mg_level, ens_mg_apply and
+ * ens_mgpcg_solve on such a workspace with other values return ENS_EINVAL.
  *
  * Bytes of caller workspace the calls below need (0 when unsupported). */
 size_t ens_mg_workspace_size(const ens_problem *p, int S, int E, int mixed);
@@ -275,6 +281,28 @@ int ens_adjoint_grad(ens_handle h, const ens_problem *p, int S, int E, const dou
                      const double *u, const double *lam, double *grad, void *work,
                      size_t work_bytes, void *stream);
 
+/* Bytes of caller workspace ens_adjoint_solve_grad needs (0 for bad arguments
+ * or a finite-element problem). */
+size_t ens_adjoint_solve_workspace_size(const ens_problem *p, int S, int E);
+
+/* The adjoint solve and the gradient in one call: given the forward solutions
+ * u[E][J][S] of A(xi) u = b (ens_pcg_solve), assembles A(xi) (ens_assemble),
+ * solves the adjoint systems A(xi) lam = w for every active lane by the
+ * ensemble Jacobi-PCG of ens_pcg_solve (x = 0 start, rtol, maxit, frozen lanes,
+ * per-lane status), and writes
+ *   Q[E][S] = w^T u (ens_qoi with weights),
+ *   grad[E][S][nparam] = dQ/dxi = -lam^T (dA/dxi) u (ens_adjoint_grad),
+ *   lam[E][J][S], iters[E][S], relres[E][S], status[E][S] of the adjoint solve.
+ * w[J] (device) is the functional's weight vector; active as for ens_pcg_solve
+ * (NULL = all lanes).  The assembled values, the adjoint right-hand side and
+ * the solver's scratch live in work (ens_adjoint_solve_workspace_size bytes).
+ * FD5 and FD7 problems only (ENS_ENOTSUP otherwise).  No synchronisation. */
+int ens_adjoint_solve_grad(ens_handle h, const ens_problem *p, int S, int E, const double *xi,
+                           const int32_t *rowptr, const int32_t *colidx, const double *u,
+                           const double *w, const uint8_t *active, double rtol, int maxit, double *Q,
+                           double *grad, double *lam, int32_t *iters, double *relres, int32_t *status,
+                           void *work, size_t work_bytes, void *stream);
+
 /* Bytes of caller workspace ens_pcg_solve_ir needs. */
 size_t ens_pcg_ir_workspace_size(int J, int64_t nnz, int S, int E);
 
@@ -314,7 +342,10 @@ int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E,
  * The caller still provides every input and output, as for ens_pcg_solve.
  *   - It runs on the calling thread's current device.  Its first call on a
  *     device looks up the array's device address there (once per device);
- *     make that first call before any stream capture.
+ *     make that first call before any stream capture.  The address is kept
+ *     for the life of the process: after cudaDeviceReset on a device (which
+ *     unloads the library's device code there) this entry point must not be
+ *     called on that device again.
  *   - It calls no cudaMalloc, cudaFree or allocating library routine, and
  *     instantiates no CUDA graph: the iteration is launched from the host,
  *     which reads the live-lane count back every 16 trips (so the call
@@ -394,6 +425,24 @@ int ens_sg_refine(int N, int M, const int8_t *lvl, const int32_t *idx, int first
  * alpha(l) = |l|): the 2^N corners (corner c has i_n = bit n of c), then
  * `level` refinement rounds of every newest point.  Returns the count. */
 int ens_sg_initial(int N, int level, int max_out, int8_t *lvl, int32_t *idx);
+
+/* (host) Coordinates of M grid points (Section 2.2, the 1-D points
+ * y_{l,i} = i 2^(1-l) - 1 of the hierarchical basis, taken per dimension):
+ * y[m][n] = idx[m][n] 2^(1 - lvl[m][n]) - 1, exact (dyadic).  lvl[M][N],
+ * idx[M][N] and y[M][N] are host memory; ENS_EINVAL for a level outside
+ * [0, 62] or a NULL array with M > 0. */
+int ens_sg_points(int N, int M, const int8_t *lvl, const int32_t *idx, double *y);
+
+/* Measurement aid (no counterpart in the paper): the FP64 issue rate, which
+ * bounds the ensemble SpMV and the PCG vector kernels on GB300.  Launches
+ * `blocks` blocks of 256 threads, each thread running eight independent FP64
+ * fused multiply-add recurrences for `iters` steps, on `stream`; sink[blocks]
+ * (device f64) is written only in a case that never occurs (it keeps the
+ * work from being optimised away).  Time the launch with events on `stream`;
+ * ens_fp64_peak_flops gives its floating-point operations (2 per fused
+ * multiply-add). */
+int ens_fp64_peak(ens_handle h, int blocks, int iters, double *sink, void *stream);
+double ens_fp64_peak_flops(int blocks, int iters);
 
 #ifdef __cplusplus
 }

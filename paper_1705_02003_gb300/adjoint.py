@@ -3,8 +3,9 @@ torch.autograd.Function, with the gradient from one adjoint ensemble solve.
 
 forward:  assemble A(xi_s) for all samples (K1), solve A u = b in ensembles
           (K2-K4), Q_s = w^T u_s (ens_qoi).
-backward: solve A lambda = w with the same kernels (A is symmetric), then
-          dQ/dxi = -lambda^T (dA/dxi) u (ens_adjoint_grad, K8), times dL/dQ.
+backward: one call of ens_adjoint_solve_grad: solve A lambda = w with the same
+          kernels (A is symmetric), then dQ/dxi = -lambda^T (dA/dxi) u (K8),
+          times dL/dQ.
 
 With recompute=True the forward solutions are not kept between forward and
 backward: backward solves for u again (the memory of one set of solution
@@ -53,7 +54,7 @@ class AdjointSolver:
         self.grad = torch.empty(L * self.N, **f64)
         self.work = torch.empty(ens.ens_pcg_workspace_size(self.J, self.nnz, self.S, self.Emax), dtype=torch.uint8,
                                 device=dev)
-        self.gwork = torch.empty(ens.ens_adjoint_workspace_size(prob, self.S, self.Emax), dtype=torch.uint8,
+        self.gwork = torch.empty(ens.ens_adjoint_solve_workspace_size(prob, self.S, self.Emax), dtype=torch.uint8,
                                  device=dev)
         self.last = {}
 
@@ -72,12 +73,10 @@ class AdjointSolver:
             self.active[M:L].fill_(0)
         return M, E, L
 
-    def _solve(self, E, L, rhs_w: bool, out):
+    def _solve(self, E, L, out):
         J, S, nnz = self.J, self.S, self.nnz
         vals, dinv, b = self.vals[: E * nnz * S], self.dinv[: E * J * S], self.b[: E * J * S]
         ens.ens_assemble(self.h, self.prob, S, E, self.xi[: L * self.N], self.rowptr, self.colidx, vals, dinv, b)
-        if rhs_w:
-            b.view(E, J, S).copy_(self.w.view(1, J, 1).expand(E, J, S))
         ens.ens_pcg_solve(self.h, J, nnz, S, E, self.rowptr, self.colidx, vals, dinv, b, out[: E * J * S],
                           self.active[:L], self.rtol, self.maxit, self.iters[:L], self.relres[:L], self.status[:L],
                           self.work)
@@ -85,7 +84,7 @@ class AdjointSolver:
     def forward(self, xi: torch.Tensor) -> torch.Tensor:
         """Q[M] for the samples xi[M][N] (device f64)."""
         M, E, L = self._load(xi)
-        self._solve(E, L, False, self.u)
+        self._solve(E, L, self.u)
         ens.ens_qoi(self.h, self.J, self.S, E, self.u[: E * self.J * self.S], self.q[:L], w=self.w)
         self.last = dict(forward_iters=self.iters[:M].clone(), forward_status=self.status[:M].clone())
         return self.q[:M].clone()
@@ -94,12 +93,14 @@ class AdjointSolver:
         """dQ/dxi [M][N]; solves for u again first when recompute_forward."""
         M, E, L = self._load(xi)
         if recompute_forward:
-            self._solve(E, L, False, self.u)
-        self._solve(E, L, True, self.lam)
+            self._solve(E, L, self.u)
+        n = E * self.J * self.S
+        ens.ens_adjoint_solve_grad(self.h, self.prob, self.S, E, self.xi[: L * self.N], self.rowptr, self.colidx,
+                                   self.u[:n], self.w, self.active[:L], self.rtol, self.maxit, self.q[:L],
+                                   self.grad[: L * self.N], self.lam[:n], self.iters[:L], self.relres[:L],
+                                   self.status[:L], self.gwork)
         self.last["adjoint_iters"] = self.iters[:M].clone()
         self.last["adjoint_status"] = self.status[:M].clone()
-        ens.ens_adjoint_grad(self.h, self.prob, self.S, E, self.xi[: L * self.N], self.u[: E * self.J * self.S],
-                             self.lam[: E * self.J * self.S], self.grad[: L * self.N], self.gwork)
         return self.grad[: M * self.N].view(M, self.N).clone()
 
 

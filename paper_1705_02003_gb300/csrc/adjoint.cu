@@ -16,6 +16,7 @@
 // partials in block order (deterministic).
 #include "ens_common.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace ens {
@@ -190,4 +191,90 @@ extern "C" int ens_adjoint_grad(ens_handle h, const ens_problem *p, int S, int E
                                                     grad);
     ENS_LAUNCH_CHECK(h, "ens_adjoint_grad");
     return ENS_OK;
+}
+
+namespace ens {
+namespace {
+
+// b[e][j][s] = w[j]: the adjoint right-hand side of every lane.
+__global__ void k_broadcast_w(int J, int S, int E, const double *__restrict__ w, double *__restrict__ b)
+{
+    const size_t n = (size_t)E * J * S;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = w[(i / S) % J];
+}
+
+struct AdjWs {
+    double *vals, *dinv, *b;
+    void *pcg, *grad;
+    size_t pcg_bytes, grad_bytes, total;
+};
+
+AdjWs adj_layout(const ens_problem *p, int J, int64_t nnz, int S, int E, char *base)
+{
+    AdjWs w;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        void *ptr = base ? base + off : nullptr;
+        off = align256(off + bytes);
+        return ptr;
+    };
+    w.vals = (double *)take((size_t)E * nnz * S * sizeof(double));
+    w.dinv = (double *)take((size_t)E * J * S * sizeof(double));
+    w.b = (double *)take((size_t)E * J * S * sizeof(double));
+    w.pcg_bytes = ens_pcg_workspace_size(J, nnz, S, E);
+    w.pcg = take(w.pcg_bytes);
+    w.grad_bytes = ens_adjoint_workspace_size(p, S, E);
+    w.grad = take(w.grad_bytes);
+    w.total = off;
+    return w;
+}
+
+}  // namespace
+}  // namespace ens
+
+extern "C" size_t ens_adjoint_solve_workspace_size(const ens_problem *p, int S, int E)
+{
+    int J;
+    int64_t nnz;
+    std::string why;
+    if (problem_check(p, &J, &nnz, &why) || !lane_count_ok(S) || E <= 0) return 0;
+    if (p->kind != ENS_FD5_LOGKL && p->kind != ENS_FD7_AXIS) return 0;
+    return adj_layout(p, J, nnz, S, E, nullptr).total;
+}
+
+extern "C" int ens_adjoint_solve_grad(ens_handle h, const ens_problem *p, int S, int E, const double *xi,
+                                      const int32_t *rowptr, const int32_t *colidx, const double *u,
+                                      const double *w, const uint8_t *active, double rtol, int maxit, double *Q,
+                                      double *grad, double *lam, int32_t *iters, double *relres, int32_t *status,
+                                      void *work, size_t work_bytes, void *stream)
+{
+    if (!h) return ENS_EINVAL;
+    int J;
+    int64_t nnz;
+    std::string why;
+    int rc = problem_check(p, &J, &nnz, &why);
+    if (rc) return set_error(h, rc, "ens_adjoint_solve_grad: " + why);
+    if (p->kind != ENS_FD5_LOGKL && p->kind != ENS_FD7_AXIS)
+        return set_error(h, ENS_ENOTSUP, "ens_adjoint_solve_grad: only the FD problems have an adjoint gradient here");
+    if (!lane_count_ok(S) || E < 0 || E > 65535) return set_error(h, ENS_EINVAL, "ens_adjoint_solve_grad: bad S / E");
+    if (E == 0) return ENS_OK;
+    if (!xi || !rowptr || !colidx || !u || !w || !Q || !grad || !lam || !iters || !relres || !status || !work)
+        return set_error(h, ENS_EINVAL, "ens_adjoint_solve_grad: null pointer");
+    if (work_bytes < ens_adjoint_solve_workspace_size(p, S, E))
+        return set_error(h, ENS_ENOMEM, "ens_adjoint_solve_grad: workspace too small");
+    AdjWs ws = adj_layout(p, J, nnz, S, E, (char *)work);
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = ens_assemble(h, p, S, E, xi, rowptr, colidx, ws.vals, 0, ws.dinv, nullptr, stream);
+    if (rc) return rc;
+    const size_t n = (size_t)E * J * S;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 16);
+    k_broadcast_w<<<blocks, 256, 0, st>>>(J, S, E, w, ws.b);
+    ENS_LAUNCH_CHECK(h, "ens_adjoint_solve_grad (right-hand side)");
+    rc = ens_pcg_solve(h, J, nnz, S, E, rowptr, colidx, ws.vals, ws.dinv, ws.b, lam, active, rtol, maxit, iters,
+                       relres, status, ws.pcg, ws.pcg_bytes, stream);
+    if (rc) return rc;
+    rc = ens_qoi(h, J, S, E, u, w, Q, stream);
+    if (rc) return rc;
+    return ens_adjoint_grad(h, p, S, E, xi, u, lam, grad, ws.grad, ws.grad_bytes, stream);
 }

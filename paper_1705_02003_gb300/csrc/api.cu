@@ -148,3 +148,17 @@ extern "C" int ens_sg_initial(int N, int level, int max_out, int8_t *lvl, int32_
     }
     return M;
 }
+
+extern "C" int ens_sg_points(int N, int M, const int8_t *lvl, const int32_t *idx, double *y)
+{
+    if (N < 1 || M < 0) return ENS_EINVAL;
+    if (M > 0 && (!lvl || !idx || !y)) return ENS_EINVAL;
+    for (size_t k = 0; k < (size_t)M * N; k++) {
+        const int l = lvl[k];
+        if (l < 0 || l > 62) return ENS_EINVAL;
+        // y = i 2^(1-l) - 1: the product is a power-of-two scaling and the
+        // difference of two dyadic numbers of at most 63 bits, so both are exact
+        y[k] = std::ldexp((double)idx[k], 1 - l) - 1.0;
+    }
+    return ENS_OK;
+}

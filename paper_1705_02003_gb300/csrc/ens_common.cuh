@@ -19,6 +19,13 @@ struct GraphEntry {
     uint64_t last_use = 0;
 };
 
+// The problem, S, E and precision a multigrid workspace was set up with (its
+// layout depends on them).
+struct MgTag {
+    const void *work = nullptr;
+    int kind = 0, n = 0, S = 0, E = 0, mixed = 0;
+};
+
 }  // namespace ens
 
 struct ens_ctx {
@@ -33,6 +40,7 @@ struct ens_ctx {
     int *check_flag = nullptr;               // device word for the graph check
     void *sort_scratch = nullptr;            // device-wide sort of more than 16384 keys (grown on demand)
     size_t sort_scratch_bytes = 0;
+    std::vector<ens::MgTag> mg_tags;         // multigrid workspaces set up on this handle (the last 16)
 };
 
 namespace ens {

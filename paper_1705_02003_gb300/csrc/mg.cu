@@ -24,13 +24,18 @@
 // the power-of-two weights are exact), so it reproduces a plain host
 // computation bit for bit; the V-cycle itself uses fused multiply-adds.  With
 // `mixed` the hierarchy is also rounded once to float and the V-cycle runs in
-// float (the same kernels instantiated on float); CG stays in double.
+// float (the same kernels instantiated on float); CG stays in double.  Each
+// lane's input is scaled by a power of two that brings its largest entry
+// below 2 before the rounding to float, and the result is scaled back: exact,
+// and the V-cycle commutes with it, so lanes of any magnitude FP64 holds
+// stay inside float's range.
 //
 // Layout: every vector of level l is [E][J_l][S] f64, every matrix
 // [E][nnz_l][S] f64 (level 0 is the caller's), the coarsest operator's
 // inverse [E][729][S].  Per-sample scalars are [E][S].
 #include "ens_common.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace ens {
@@ -61,6 +66,7 @@ struct MgWork {
     MgLevel lv[kMgMaxLev];
     double *cinv = nullptr;  // [E][27 * 27][S]: inverse of the coarsest operator
     float *cinv32 = nullptr;
+    unsigned long long *rmax = nullptr;  // [E][S] per-lane largest |r| of the float V-cycle's input
     int mixed = 0;           // the V-cycle runs in float on a float copy of the hierarchy
     int *bad = nullptr;      // [E][S]
     // CG state
@@ -141,6 +147,7 @@ bool mg_layout(const ens_problem *p, int S, int E, int mixed, char *base, MgWork
             }
         }
         w->cinv32 = (float *)take(ES * kInv * sizeof(float));
+        w->rmax = (unsigned long long *)take(ES * sizeof(unsigned long long));
     }
     w->bad = (int *)take(ES * sizeof(int));
     const int J = w->lv[0].J;
@@ -517,6 +524,54 @@ __global__ void k_mg_convert(size_t n, size_t per_ens, const A *__restrict__ src
     }
 }
 
+// Per-lane largest magnitude of a double vector [E][J][S] (as the bits of a
+// non-negative double, whose integer order is the numeric order), for the
+// power-of-two scaling of the float V-cycle's input.  mx[E][S] starts at 0.
+__global__ void k_mg_lane_max(int J, int S, const double *__restrict__ r, unsigned long long *mx,
+                              const int *__restrict__ ens_live)
+{
+    const int e = blockIdx.y;
+    if (ens_live && ens_live[e] == 0) return;
+    const int s = threadIdx.x % S, g = threadIdx.x / S, G = blockDim.x / S;
+    const double *re = r + (size_t)e * J * S + s;
+    double m = 0.0;
+    for (int j = blockIdx.x * G + g; j < J; j += gridDim.x * G) m = fmax(m, fabs(re[(size_t)j * S]));
+    __shared__ double sh[kBlock];
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x < S) {
+        for (int q = 1; q < G; q++) m = fmax(m, sh[q * S + threadIdx.x]);
+        // NaN compares false in fmax; a lane with a NaN residual keeps its own value
+        if (m > 0.0) atomicMax(mx + (size_t)e * S + threadIdx.x, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// The power of two 2^x of a lane's scale: x = the binary exponent of its
+// largest magnitude (0 for a zero or non-finite lane), so the scaled values lie
+// below 2 in magnitude and their float rounding neither overflows nor leaves
+// the normal range for entries within 2^-125 of the largest.
+__device__ __forceinline__ int lane_exponent(const unsigned long long *mx, size_t L)
+{
+    const double m = __longlong_as_double((long long)mx[L]);
+    return (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
+}
+
+// dst = float(src 2^-x) per lane (narrow) or dst = double(src) 2^x (widen).
+// Scaling by a power of two is exact, and every operation of the V-cycle
+// commutes with it, so in range the result equals the unscaled one bit for bit.
+template <typename A, typename B>
+__global__ void k_mg_convert_scaled(size_t n, size_t per_ens, int S, const A *__restrict__ src, B *__restrict__ dst,
+                                    const unsigned long long *__restrict__ mx, int widen,
+                                    const int *__restrict__ ens_live)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = t / per_ens;
+        if (ens_live && ens_live[e] == 0) continue;
+        const int x = lane_exponent(mx, e * S + t % S);
+        dst[t] = (B)scalbn((double)src[t], widen ? x : -x);
+    }
+}
+
 // ---- CG kernels: 256-row blocks, per-lane block partial sums ---------------------
 
 // Per-lane sum over the block's row groups, pairwise in a fixed order; the
@@ -735,8 +790,32 @@ __global__ void k_mgcg_final(CgArgs a, int kind, const double *__restrict__ part
 
 inline dim3 rl_grid(int J, int S, int E) { return dim3((unsigned)((J + kBlock / S - 1) / (kBlock / S)), (unsigned)E); }
 
+// The workspace's set-up record on this handle (nullptr if it has none).
+MgTag *mg_tag(ens_ctx *h, const void *work)
+{
+    for (auto &t : h->mg_tags)
+        if (t.work == work) return &t;
+    return nullptr;
+}
+
+void mg_record(ens_ctx *h, const ens_problem *p, int S, int E, int mixed, const void *work)
+{
+    MgTag *t = mg_tag(h, work);
+    if (!t) {
+        if (h->mg_tags.size() >= 16) h->mg_tags.erase(h->mg_tags.begin());
+        h->mg_tags.push_back(MgTag());
+        t = &h->mg_tags.back();
+    }
+    t->work = work;
+    t->kind = p->kind;
+    t->n = p->n;
+    t->S = S;
+    t->E = E;
+    t->mixed = mixed;
+}
+
 int mg_check(ens_ctx *h, const char *who, const ens_problem *p, int S, int E, int mixed, const void *work,
-             size_t work_bytes, MgWork *w)
+             size_t work_bytes, MgWork *w, bool setup = false)
 {
     if (!h) return ENS_EINVAL;
     if (!p) return set_error(h, ENS_EINVAL, std::string(who) + ": null problem");
@@ -751,6 +830,12 @@ int mg_check(ens_ctx *h, const char *who, const ens_problem *p, int S, int E, in
     if (!mg_layout(p, S, E, mixed, nullptr, w))
         return set_error(h, ENS_EINVAL, std::string(who) + ": n must be 2^k - 1 (k >= 2)");
     if (E > 0 && (!work || work_bytes < w->bytes)) return set_error(h, ENS_EINVAL, std::string(who) + ": workspace too small");
+    if (!setup && E > 0) {
+        const MgTag *t = mg_tag(h, work);
+        if (t && (t->kind != p->kind || t->n != p->n || t->S != S || t->E != E || t->mixed != mixed))
+            return set_error(h, ENS_EINVAL, std::string(who) + ": the workspace was set up (ens_mg_setup) with another "
+                                            "problem, S, E or mixed flag");
+    }
     mg_layout(p, S, E, mixed, (char *)work, w);
     return ENS_OK;
 }
@@ -828,11 +913,17 @@ int mg_precond(ens_ctx *h, const MgWork &w, const int32_t *rp0, const int32_t *c
                int E, const double *r, double *z, const int *ens_live, cudaStream_t st)
 {
     if (!w.mixed) return mg_vcycle<double>(h, w, rp0, ci0, vals0, S, E, r, z, ens_live, st);
-    const size_t per = (size_t)w.lv[0].J * S, n = per * E;
-    k_mg_convert<double, float><<<convert_blocks(n), kBlock, 0, st>>>(n, per, r, w.lv[0].rhs32, ens_live);
+    const int J = w.lv[0].J;
+    const size_t per = (size_t)J * S, n = per * E;
+    ENS_CUDA_CHECK(h, cudaMemsetAsync(w.rmax, 0, sizeof(unsigned long long) * E * S, st));
+    const unsigned nb = (unsigned)std::min<int>((J + kBlock / S - 1) / (kBlock / S), 64);
+    k_mg_lane_max<<<dim3(nb, (unsigned)E), kBlock, 0, st>>>(J, S, r, w.rmax, ens_live);
+    k_mg_convert_scaled<double, float><<<convert_blocks(n), kBlock, 0, st>>>(n, per, S, r, w.lv[0].rhs32, w.rmax, 0,
+                                                                             ens_live);
     const int rc = mg_vcycle<float>(h, w, rp0, ci0, w.lv[0].vals32, S, E, w.lv[0].rhs32, w.lv[0].e32, ens_live, st);
     if (rc) return rc;
-    k_mg_convert<float, double><<<convert_blocks(n), kBlock, 0, st>>>(n, per, w.lv[0].e32, z, ens_live);
+    k_mg_convert_scaled<float, double><<<convert_blocks(n), kBlock, 0, st>>>(n, per, S, w.lv[0].e32, z, w.rmax, 1,
+                                                                             ens_live);
     ENS_LAUNCH_CHECK(h, "multigrid V-cycle (float)");
     return ENS_OK;
 }
@@ -859,10 +950,11 @@ extern "C" int ens_mg_setup(ens_handle h, const ens_problem *p, int S, int E, in
                             const int32_t *colidx, const double *vals, void *work, size_t work_bytes, void *stream)
 {
     MgWork w;
-    int rc = mg_check(h, "ens_mg_setup", p, S, E, mixed, work, work_bytes, &w);
+    int rc = mg_check(h, "ens_mg_setup", p, S, E, mixed, work, work_bytes, &w, true);
     if (rc) return rc;
     if (E == 0) return ENS_OK;
     if (!rowptr || !colidx || !vals) return set_error(h, ENS_EINVAL, "ens_mg_setup: null pointer");
+    mg_record(h, p, S, E, mixed, work);
     cudaStream_t st = (cudaStream_t)stream;
     const int ES = E * S;
     for (int l = 1; l < w.L; l++) {

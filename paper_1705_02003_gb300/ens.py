@@ -27,7 +27,9 @@ EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "e
            "ens_pcg_solve_static", "ens_pcg_ir_workspace_size", "ens_pcg_solve_ir",
            "ens_adjoint_workspace_size", "ens_adjoint_grad", "ens_param_indicator",
            "ens_stream_workspace_size", "ens_solve_stream", "ens_pcg_branches", "ens_check_pattern",
-           "ens_mg_workspace_size", "ens_mg_setup", "ens_mg_level", "ens_mg_apply", "ens_mgpcg_solve")
+           "ens_mg_workspace_size", "ens_mg_setup", "ens_mg_level", "ens_mg_apply", "ens_mgpcg_solve",
+           "ens_sg_points", "ens_fp64_peak", "ens_fp64_peak_flops", "ens_adjoint_solve_workspace_size",
+           "ens_adjoint_solve_grad")
 
 _lib = None
 _lock = threading.Lock()
@@ -100,6 +102,10 @@ def _declare(L):
     L.ens_adjoint_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
     L.ens_adjoint_workspace_size.restype = c.c_size_t
     L.ens_adjoint_grad.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, c.c_size_t, vp]
+    L.ens_adjoint_solve_workspace_size.argtypes = [c.POINTER(Problem), c.c_int, c.c_int]
+    L.ens_adjoint_solve_workspace_size.restype = c.c_size_t
+    L.ens_adjoint_solve_grad.argtypes = [vp, c.POINTER(Problem), c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, c.c_double,
+                                         c.c_int, vp, vp, vp, vp, vp, vp, vp, c.c_size_t, vp]
     L.ens_pcg_ir_workspace_size.argtypes = [c.c_int, c.c_int64, c.c_int, c.c_int]
     L.ens_pcg_ir_workspace_size.restype = c.c_size_t
     L.ens_pcg_solve_ir.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp, vp,
@@ -112,6 +118,10 @@ def _declare(L):
     L.ens_sg_refine.argtypes = [c.c_int, c.c_int, i8p, i32p, c.c_int, f64p, c.c_double, c.c_int,
                                 c.c_int, i8p, i32p]
     L.ens_sg_initial.argtypes = [c.c_int, c.c_int, c.c_int, i8p, i32p]
+    L.ens_sg_points.argtypes = [c.c_int, c.c_int, i8p, i32p, f64p]
+    L.ens_fp64_peak.argtypes = [vp, c.c_int, c.c_int, vp, vp]
+    L.ens_fp64_peak_flops.argtypes = [c.c_int, c.c_int]
+    L.ens_fp64_peak_flops.restype = c.c_double
 
 
 def _ptr(t):
@@ -408,6 +418,29 @@ def ens_adjoint_grad(h: Handle, prob: Problem, S: int, E: int, xi, u, lam, grad,
     h.check(rc, "ens_adjoint_grad")
 
 
+def ens_adjoint_solve_workspace_size(prob: Problem, S: int, E: int) -> int:
+    return int(load().ens_adjoint_solve_workspace_size(ctypes.byref(prob), int(S), int(E)))
+
+
+def ens_adjoint_solve_grad(h: Handle, prob: Problem, S: int, E: int, xi, rowptr, colidx, u, w, active,
+                           rtol: float, maxit: int, Q, grad, lam, iters, relres, status, work, stream=None):
+    """Adjoint solve A lam = w, Q = w^T u and dQ/dxi = -lam^T (dA/dxi) u per lane."""
+    J, _ = ens_problem_size(prob)
+    for t, nm, dt in ((xi, "xi", torch.float64), (u, "u", torch.float64), (w, "w", torch.float64),
+                      (Q, "Q", torch.float64), (grad, "grad", torch.float64), (lam, "lam", torch.float64),
+                      (iters, "iters", torch.int32), (relres, "relres", torch.float64),
+                      (status, "status", torch.int32)):
+        _check_dtype(t, dt, nm)
+    if (u.numel() != E * J * S or lam.numel() != E * J * S or w.numel() != J or grad.numel() != E * S * prob.nparam
+            or Q.numel() != E * S or iters.numel() != E * S):
+        raise ValueError("array sizes do not match E, J, S, nparam")
+    rc = load().ens_adjoint_solve_grad(h.ptr, ctypes.byref(prob), int(S), int(E), _ptr(xi), _ptr(rowptr),
+                                       _ptr(colidx), _ptr(u), _ptr(w), _ptr(active), float(rtol), int(maxit),
+                                       _ptr(Q), _ptr(grad), _ptr(lam), _ptr(iters), _ptr(relres), _ptr(status),
+                                       _ptr(work), work.numel(), _stream(stream))
+    h.check(rc, "ens_adjoint_solve_grad")
+
+
 STATIC_SCRATCH_BYTES = 8 << 20
 
 
@@ -514,3 +547,23 @@ def ens_sg_initial(N: int, level: int, max_out: int = 1 << 16):
     if M < 0:
         raise EnsError(f"ens_sg_initial failed ({M})")
     return lvl[:M].copy(), idx[:M].copy()
+
+
+def ens_sg_points(lvl, idx) -> np.ndarray:
+    """(host) y[m][n] = idx 2^(1 - lvl) - 1 of the grid points (exact)."""
+    lvl = np.ascontiguousarray(lvl, np.int8)
+    idx = np.ascontiguousarray(idx, np.int32)
+    M, N = lvl.shape
+    y = np.zeros((M, N), np.float64)
+    rc = load().ens_sg_points(int(N), int(M), lvl, idx, y)
+    if rc != OK:
+        raise EnsError(f"ens_sg_points failed ({rc})")
+    return y
+
+
+def ens_fp64_peak(h: "Handle", blocks: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """Launch the FP64 fused multiply-add throughput kernel; returns its
+    floating-point operation count (time it with events on the stream)."""
+    _check_dtype(sink, torch.float64, "sink")
+    h.check(load().ens_fp64_peak(h.ptr, int(blocks), int(iters), _ptr(sink), _stream(stream)), "ens_fp64_peak")
+    return float(load().ens_fp64_peak_flops(int(blocks), int(iters)))

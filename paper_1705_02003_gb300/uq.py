@@ -29,8 +29,8 @@ from .solver import EnsembleSolver
 
 
 def coords(lvl: np.ndarray, idx: np.ndarray) -> np.ndarray:
-    """y_{l,i} = i 2^(1-l) - 1 (exact: dyadic)."""
-    return idx.astype(np.float64) * np.exp2(1.0 - lvl.astype(np.float64)) - 1.0
+    """Grid-point coordinates y_{l,i} = i 2^(1-l) - 1 per dimension (ens_sg_points)."""
+    return ens.ens_sg_points(lvl, idx)
 
 
 def work_ratio(S: int, perm: np.ndarray, iters: np.ndarray) -> float:

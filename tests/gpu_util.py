@@ -92,3 +92,24 @@ class Case:
         E, S = self.E, self.S
         a = np.asarray(per_lane, np.float64).reshape(E, S, J).transpose(0, 2, 1).copy()
         return torch.from_numpy(a.ravel()).to("cuda")
+
+
+def elem_err(x, x0):
+    """max_j |x_j - x0_j| / max_j |x0_j|: an element-wise bound relative to the
+    largest entry (a relative 2-norm could hide large errors in small entries)."""
+    x, x0 = np.asarray(x), np.asarray(x0)
+    return float(np.max(np.abs(x - x0)) / np.max(np.abs(x0)))
+
+
+def grouping_on_oracle_counts(h, r):
+    """Feed the oracle run's grid and iteration surpluses to ens_group level by
+    level; predictions and permutations must equal the oracle's bit for bit."""
+    S = r["S"]
+    for (a, b), pred_o, perm_o in zip(r["levels"][1:], r["pred"][1:], r["perms"]["sur"][1:]):
+        yq = O.sg_points(r["lvl"][a:b], r["idx"][a:b])
+        pred = torch.empty(b - a, dtype=torch.float64, device="cuda")
+        perm = torch.empty(b - a, dtype=torch.int32, device="cuda")
+        dev = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+        ens.ens_group(h, dev(r["lvl"][:a]), dev(r["idx"][:a]), dev(r["cI"][:a]), dev(yq), S, pred, perm)
+        assert np.array_equal(pred.cpu().numpy(), pred_o)
+        assert np.array_equal(perm.cpu().numpy(), perm_o)

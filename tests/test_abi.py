@@ -70,6 +70,29 @@ def test_initial_grid_bit_exact(N, L):
     np.testing.assert_array_equal(uq.coords(*a), O.sg_points(*b))
 
 
+def test_grid_points_bit_exact_and_checked():
+    """ens_sg_points gives the oracle's coordinates bit for bit on refined grids
+    of every dimension, and refuses levels outside [0, 62]."""
+    rng = np.random.default_rng(12)
+    for N in (1, 2, 4, 6, 8):
+        lvl, idx = O.sg_initial(N, 3 if N <= 4 else 1)
+        first = 0
+        for _ in range(2):
+            nl, ni = O.sg_refine(lvl, idx, first, rng.standard_normal(len(lvl)), 1.0, 40)
+            first = len(lvl)
+            lvl, idx = np.concatenate([lvl, nl]), np.concatenate([idx, ni])
+        assert np.array_equal(ens.ens_sg_points(lvl, idx), O.sg_points(lvl, idx))
+    assert ens.ens_sg_points(np.zeros((0, 3), np.int8), np.zeros((0, 3), np.int32)).shape == (0, 3)
+    with pytest.raises(ens.EnsError):
+        ens.ens_sg_points(np.full((1, 2), -1, np.int8), np.ones((1, 2), np.int32))
+
+
+def test_fp64_peak_flop_count():
+    """The throughput kernel's operation count: 2 flops x 8 chains per thread
+    and step, 256 threads per block."""
+    assert ens.load().ens_fp64_peak_flops(3, 5) == 2 * 8 * 5 * 3 * 256
+
+
 def test_refinement_bit_exact():
     rng = np.random.default_rng(9)
     for N in (2, 3, 4, 6):
@@ -122,7 +145,8 @@ def test_entry_points_refuse_null_arguments_without_crashing():
     L = ens.load()
     skip = {"ens_create", "ens_last_error", "ens_problem_size", "ens_pcg_workspace_size",
             "ens_pcg_ir_workspace_size", "ens_stream_workspace_size", "ens_adjoint_workspace_size",
-            "ens_sg_refine", "ens_sg_initial", "ens_mg_workspace_size"}
+            "ens_sg_refine", "ens_sg_initial", "ens_mg_workspace_size", "ens_adjoint_solve_workspace_size",
+            "ens_sg_points", "ens_fp64_peak_flops"}
     for name in ens.EXPORTS:
         if name in skip:
             continue

@@ -102,3 +102,47 @@ def test_fem_problems_have_no_adjoint(h, kind, aniso):
     with pytest.raises(ens.EnsError, match="only the FD problems"):
         ens.ens_adjoint_grad(h, p, 2, 1, torch.zeros(8, dtype=torch.float64, device="cuda"), z, z,
                              torch.zeros(8, dtype=torch.float64, device="cuda"), work)
+
+
+def test_adjoint_solve_grad_equals_the_split_calls(h):
+    """ens_adjoint_solve_grad (assembly, adjoint solve, Q and gradient in one
+    call) gives bit for bit what the separate entry points give: ens_assemble,
+    ens_pcg_solve with right-hand side w, ens_qoi and ens_adjoint_grad."""
+    n, N, aniso, S, M = 20, 8, 3.0, 8, 11
+    prob = ens.problem("fd5", n, N, aniso)
+    w = torch.from_numpy(inputs.region_weights(n, 2)).cuda()
+    x = torch.from_numpy(inputs.draws(M, N, seed=62)).cuda()
+    sol = adjoint.AdjointSolver(h, prob, S, M, w.cpu(), 1e-11, 100000)
+    q = sol.forward(x)
+    g = sol.gradient(x, recompute_forward=False)
+    lam = sol.lam.clone()
+    E, J = sol.Emax, sol.J
+    L = E * S
+    vals = torch.empty(E * sol.nnz * S, dtype=torch.float64, device="cuda")
+    dinv = torch.empty(E * J * S, dtype=torch.float64, device="cuda")
+    ens.ens_assemble(h, prob, S, E, sol.xi[: L * N], sol.rowptr, sol.colidx, vals, dinv)
+    b = w.view(1, J, 1).expand(E, J, S).contiguous().view(-1)
+    lam2 = torch.empty(E * J * S, dtype=torch.float64, device="cuda")
+    it2 = torch.empty(L, dtype=torch.int32, device="cuda")
+    st2, rr2 = torch.empty_like(it2), torch.empty(L, dtype=torch.float64, device="cuda")
+    work = torch.empty(ens.ens_pcg_workspace_size(J, sol.nnz, S, E), dtype=torch.uint8, device="cuda")
+    ens.ens_pcg_solve(h, J, sol.nnz, S, E, sol.rowptr, sol.colidx, vals, dinv, b, lam2, sol.active[:L], 1e-11,
+                      100000, it2, rr2, st2, work)
+    g2 = torch.empty(L * N, dtype=torch.float64, device="cuda")
+    gw = torch.empty(ens.ens_adjoint_workspace_size(prob, S, E), dtype=torch.uint8, device="cuda")
+    ens.ens_adjoint_grad(h, prob, S, E, sol.xi[: L * N], sol.u, lam2, g2, gw)
+    q2 = torch.empty(L, dtype=torch.float64, device="cuda")
+    ens.ens_qoi(h, J, S, E, sol.u, q2, w=w)
+    torch.cuda.synchronize()
+    per_lane = lambda t: t[: E * J * S].view(E, J, S).permute(0, 2, 1).reshape(L, J)[:M]
+    assert torch.equal(per_lane(lam), per_lane(lam2))
+    assert torch.equal(g, g2.view(L, N)[:M])
+    assert torch.equal(sol.last["adjoint_iters"], it2[:M])
+    assert torch.equal(q, q2[:M])
+    assert torch.equal(sol.q[:M], q2[:M])
+
+
+def test_adjoint_solve_grad_refuses_fem_problems(h):
+    for kind, aniso in (("q1", 4.0), ("q1_3d_kl", 0.0)):
+        p = ens.problem(kind, 8, 4, aniso)
+        assert ens.ens_adjoint_solve_workspace_size(p, 2, 1) == 0

@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import oracle as O
+from gpu_util import grouping_on_oracle_counts
 from oracle import uq as ouq
 from paper_1705_02003_gb300 import ens, inputs, uq
 
@@ -146,6 +147,7 @@ def test_adaptive_loop_matches_oracle(h, small_run):
     assert run["levels"] == r["levels"]
     assert np.max(np.abs(run["I"] - r["I"])) <= 1
     np.testing.assert_allclose(run["G"], r["G"], rtol=1e-10)
+    grouping_on_oracle_counts(h, r)
     if np.array_equal(run["I"], r["I"]):
         for p, po in zip(run["perms"][1:], r["perms"]["sur"][1:]):
             assert np.array_equal(p, po)

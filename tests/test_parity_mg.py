@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_util import OKIND, Case
+from gpu_util import OKIND, Case, elem_err, grouping_on_oracle_counts
 from oracle import uq as ouq
 from paper_1705_02003_gb300 import ens, inputs, uq
 
@@ -88,7 +88,7 @@ def test_vcycle_matches_oracle(h, kind):
     Z = c.lane_vec(z)
     for L in range(M):
         zo = O.mg_apply(n, rp, ci, V[L], R[L])
-        assert np.linalg.norm(Z[L] - zo) <= 1e-11 * np.linalg.norm(zo), L
+        assert elem_err(Z[L], zo) <= 1e-11, L
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -112,8 +112,8 @@ def test_float_vcycle_matches_oracle(h, kind):
     for L in range(M):
         z32 = O.mg_apply32(n, rp, ci, V[L], R[L])
         z64 = O.mg_apply(n, rp, ci, V[L], R[L])
-        assert np.linalg.norm(Z[L] - z32) <= 1e-5 * np.linalg.norm(z32), L
-        assert np.linalg.norm(Z[L] - z64) <= 1e-5 * np.linalg.norm(z64), L
+        assert elem_err(Z[L], z32) <= 1e-5, L
+        assert elem_err(Z[L], z64) <= 1e-5, L
         assert not np.array_equal(Z[L], z64)  # the float path really ran
 
 
@@ -122,7 +122,7 @@ def _check(got, ref, lanes, bar):
         assert got["status"][L] == ref[j][2] == O.CONVERGED, L
         di = int(got["iters"][L]) - int(ref[j][1])
         assert abs(di) <= 1, (L, di)
-        err = np.linalg.norm(got["x"][L] - ref[j][0]) / np.linalg.norm(ref[j][0])
+        err = elem_err(got["x"][L], ref[j][0])
         assert err <= (bar if di == 0 else 1e-5), (L, err)
 
 
@@ -153,6 +153,41 @@ def test_mixed_mgpcg_matches_oracle_on_the_oracles_matrices(h, kind):
     ref = [O.mgpcg32(n, rp, ci, V[L], B[L], 1e-7, 500) for L in range(M)]
     _check(got, ref, range(M), 1e-6)
     assert all(got["status"][M:] == ens.LANE_INACTIVE)
+
+
+@pytest.mark.parametrize("shift", [-300, -140, 140, 300])
+def test_mixed_mgpcg_is_homogeneous_in_the_load(h, shift):
+    """Scaling the load by 2^shift scales every FP64 CG step and (through the
+    per-lane power-of-two scaling before the rounding to float) every float
+    V-cycle step exactly, so the mixed solve of b 2^shift returns the same
+    iterations and x 2^shift bit for bit -- also where b 2^shift lies far
+    outside float's range (2^-140 and 2^140 are about 1e-42 and 1e42)."""
+    n, S, M = 7, 8, 12
+    c = Case(h, "q1_3d_disc", n, 4, 0.0, S, draws(M, 18))
+    ref = c.solve_mg(1e-8, 200, mixed=True)
+    got = c.solve_mg(1e-8, 200, b=c.b * 2.0 ** shift, mixed=True)
+    assert np.all(ref["status"][:M] == ens.LANE_CONVERGED)
+    assert np.array_equal(got["status"], ref["status"]) and np.array_equal(got["iters"], ref["iters"])
+    assert np.array_equal(got["x"], np.ldexp(ref["x"], shift))
+
+
+def test_workspace_set_up_for_other_sizes_is_refused(h):
+    """A workspace set up with one S, E or precision and then used with another
+    is refused (its layout depends on them) instead of being read wrongly."""
+    c = Case(h, "q1_3d_kl", 7, 4, 0.0, 8, draws(16, 19))
+    work = c.mg_work(mixed=True)
+    ens.ens_mg_setup(h, c.prob, 8, c.E, c.rowptr, c.colidx, c.vals, work, mixed=False)
+    z = torch.empty_like(c.b)
+    with pytest.raises(ens.EnsError, match="set up"):
+        ens.ens_mg_apply(h, c.prob, 8, c.E, c.rowptr, c.colidx, c.vals, c.b, z, work, mixed=True)
+    J, nnz = c.J, c.nnz
+    with pytest.raises(ens.EnsError, match="set up"):
+        ens.ens_mg_apply(h, c.prob, 8, 1, c.rowptr, c.colidx, c.vals[: nnz * 8], c.b[: J * 8], z[: J * 8], work,
+                         mixed=False)
+    ens.ens_mg_apply(h, c.prob, 8, c.E, c.rowptr, c.colidx, c.vals, c.b, z, work, mixed=False)  # as set up
+    ens.ens_mg_setup(h, c.prob, 8, c.E, c.rowptr, c.colidx, c.vals, work, mixed=True)
+    ens.ens_mg_apply(h, c.prob, 8, c.E, c.rowptr, c.colidx, c.vals, c.b, z, work, mixed=True)
+    torch.cuda.synchronize()
 
 
 @pytest.mark.parametrize("name,lanes", [("q1_32c_test1", [0, 19]), ("q1_32c_test2", [1, 30])])
@@ -220,6 +255,7 @@ def test_adaptive_loop_with_multigrid_matches_oracle(h, name):
     assert run["levels"] == ref["levels"] and len(run["levels"]) >= 2
     assert np.max(np.abs(run["I"] - ref["I"])) <= 1
     np.testing.assert_allclose(run["G"], ref["G"], rtol=1e-7)
+    grouping_on_oracle_counts(h, ref)
     if np.array_equal(run["I"], ref["I"]):
         for p, po in zip(run["perms"][1:], ref["perms"]["sur"][1:]):
             assert np.array_equal(p, po)

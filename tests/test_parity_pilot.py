@@ -44,9 +44,16 @@ def test_pilot_grouping_matches_oracle_and_groups_well(h):
     assert n_ens == 256 // S
     assert sorted(perm_g.tolist()) == list(range(256))
     assert perm_g.tolist() == sorted(range(256), key=lambda i: pred_g[i])  # stable ascending sort
+    # fed the oracle's pilot counts, the GPU surrogate and grouping are the oracle's bit for bit
+    pred_o = O.sg_eval(pg.lvl, pg.idx, cI_o, draws)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    pred2 = torch.empty(256, dtype=torch.float64, device="cuda")
+    perm2 = torch.empty(256, dtype=torch.int32, device="cuda")
+    ens.ens_group(h, dev(pg.lvl), dev(pg.idx), dev(cI_o), dev(draws), S, pred2, perm2)
+    assert np.array_equal(pred2.cpu().numpy(), pred_o)
+    assert np.array_equal(perm2.cpu().numpy(), O.sort_perm(pred_o))
     if np.array_equal(I_gpu, o["iters"]):
         assert np.array_equal(pg.cI.cpu().numpy(), cI_o)
-        pred_o = O.sg_eval(pg.lvl, pg.idx, cI_o, draws)
         assert np.array_equal(pred_g, pred_o)
         assert np.array_equal(perm_g, O.sort_perm(pred_o))
 

@@ -569,7 +569,9 @@ def run_suites(h, stream, suite: str, hbm: float, fp64: float):
 
 
 def run_configs(h, stream, hbm: float, fp64: float):
-    """The ensemble SpMV (K2) on the other problem configurations, each with
+    """The ensemble SpMV (K2) on the other problem configurations, in the launch
+    shapes of their layers (the 64^3 and 512^2 problems with 1024 lanes, the
+    128^3 problem with 8 ensembles per call) and with one ensemble, each with
     inputs larger than L2: algorithmic GB/s and FP64 rate per launch."""
     import torch
 
@@ -577,7 +579,8 @@ def run_configs(h, stream, hbm: float, fp64: float):
     from paper_1705_02003_gb300.solver import EnsembleSolver
 
     out = {}
-    for name, E in (("fd7_64_batch", 4), ("fd7_128_mixed", 1), ("fd5_512_adjoint", 4)):
+    for name, E in (("fd7_64_batch", 32), ("fd7_128_mixed", 8), ("fd5_512_adjoint", 32), ("fd7_64_batch", 1),
+                    ("fd7_128_mixed", 1), ("fd5_512_adjoint", 1)):
         wl = inputs.WORKLOADS[name]
         prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
         S = 32
@@ -586,7 +589,7 @@ def run_configs(h, stream, hbm: float, fp64: float):
         t = spmv_launch(h, sol, E, xi, stream, reps=10)
         byts = E * (8 * sol.nnz * S + 4 * sol.nnz + 4 * (sol.J + 1) + 16 * sol.J * S)
         fma = E * S * (sol.nnz + sol.J)
-        out[name] = {"E": E, "S": S, "bytes_per_launch": byts, "launch_ms": t * 1e3,
+        out[f"{name}_E{E}"] = {"E": E, "S": S, "bytes_per_launch": byts, "launch_ms": t * 1e3,
                      "hbm_gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm,
                      "fp64_tflops": 2 * fma / t / 1e12, "fp64_frac": 2 * fma / t / 1e12 / fp64}
         del sol

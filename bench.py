@@ -522,25 +522,35 @@ def run_ours(args, wl):
                 json.dump(detail, fh, indent=1, default=float)
         except OSError as e:
             detail_path = f"not written ({e})"
-        arms = detail.get("arms", {})
-        line = {
-            "metric": METRIC, "value": value, "unit": "sample-solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "problem": "Q1 9-point FEM 256x256, N=4, rotated anisotropy",
-                       "J": sol.J, "nnz": sol.nnz, "S": sol.S, "samples_per_step": M,
-                       "levels": len(run["levels"]), "n_max": wl.n_max, "n_max_reading": N_MAX_READING,
-                       "rtol": wl.rtol, "grouping": "sur", "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "l2": "inputs larger than L2 (each level's values >= 225 MB)"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "path_frac": path["path_frac"],
-            "speedup_vs_per_sample": {k: arms["sur"][f"speedup_vs_{k}"]
-                                      for k in ("per_sample_serial", "per_sample_batched")} if arms else None,
-            "detail": detail_path,
-        }
+        line = compact_line(value=value, world=world, args=args, tmax=tmax, wl=wl, sol=sol, M=M,
+                            levels=len(run["levels"]), roofline=roofline, cpu=cpu, e2e=e2e,
+                            launches=launches_per_step * args.steps, clocks=clk, path_frac=path["path_frac"],
+                            arms=detail.get("arms", {}), detail_path=detail_path)
         print(json.dumps(line, separators=(",", ":")))
     return 0
+
+
+def compact_line(value, world, args, tmax, wl, sol, M, levels, roofline, cpu, e2e, launches, clocks, path_frac,
+                 arms, detail_path):
+    """The one JSON object printed last: the measured metric with its config,
+    the dominant kernel's roofline, the CPU baseline, the end-to-end figure and
+    the clocks (everything else is in the detail file)."""
+    return {
+        "metric": METRIC, "value": value, "unit": "sample-solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "problem": "Q1 9-point FEM 256x256, N=4, rotated anisotropy",
+                   "J": sol.J, "nnz": sol.nnz, "S": sol.S, "samples_per_step": M,
+                   "levels": levels, "n_max": wl.n_max, "n_max_reading": N_MAX_READING,
+                   "rtol": wl.rtol, "grouping": "sur", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (each level's values >= 225 MB)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clocks,
+        "path_frac": path_frac,
+        "speedup_vs_per_sample": {k: arms["sur"][f"speedup_vs_{k}"]
+                                  for k in ("per_sample_serial", "per_sample_batched")} if arms else None,
+        "detail": detail_path,
+    }
 
 
 def run_suites(h, stream, suite: str, hbm: float, fp64: float):

@@ -4,7 +4,7 @@
                     [--workload q1_256_adaptive] [--no-arms] [--no-cpu]
                     [--suite layers,configs,c1,pilot,paper,mixed-mg | all]
                     [--detail-out PATH]
-                    [--kernel-only [--kernel-ensembles E]]
+                    [--kernel-only [--kernel-ensembles E]] [--mg-once mg|mg32]
 
 A step is one pass of the whole path over the workload: the grid-generation
 and grouping loop of the paper's flowchart (initial sparse grid, then per
@@ -37,7 +37,8 @@ and, with --suite:
                   the Jacobi and the multigrid preconditioner
   mixed-mg        the multigrid solve with a float V-cycle on Test 1 / Test 2
 
---kernel-only times K2 alone (the case the Nsight Compute summaries use).
+--kernel-only times K2 alone and --mg-once runs one multigrid solve (the cases
+the Nsight Compute summaries use).
 --impl reference times the CPU oracle (the reference arm of this project) on
 the host cores for the same metric.  Multi-GPU runs are independent replicas
 that time the loop only.
@@ -1022,6 +1023,27 @@ def run_kernel_only(args, wl):
     return 0
 
 
+def run_mg_once(args):
+    """One multigrid-preconditioned ensemble solve of 64 draws of Section 4's
+    Test 1 (4 ensembles of 16; the CG loop is launched from the host, so a
+    kernel profiler lists every launch)."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens, inputs
+    from paper_1705_02003_gb300.solver import EnsembleSolver
+
+    h = ens.Handle(0)
+    wl = inputs.WORKLOADS["q1_32c_test1"]
+    sol = EnsembleSolver(h, ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso), 16, 64, wl.rtol, 2000,
+                         precond="mg32" if args.mg_once == "mg32" else "mg")
+    it, st, _, _ = sol.solve(torch.from_numpy(inputs.draws(64, 4, seed=1)).cuda())
+    torch.cuda.synchronize()
+    print(json.dumps({"mg_once": args.mg_once, "iters_max": int(it.max().item()),
+                      "converged": bool((st == ens.LANE_CONVERGED).all().item())}))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1038,6 +1060,8 @@ def main():
     ap.add_argument("--kernel-only", action="store_true", help="time the ensemble SpMV alone (profiling)")
     ap.add_argument("--kernel-ensembles", type=int, default=8)
     ap.add_argument("--kernel-s", type=int, default=0, help="lanes per ensemble for --kernel-only (0: the workload's)")
+    ap.add_argument("--mg-once", choices=["mg", "mg32"], default=None,
+                    help="one multigrid solve of 64 draws of Section 4's Test 1 (profiling)")
     args = ap.parse_args()
     from paper_1705_02003_gb300 import inputs
 
@@ -1046,6 +1070,8 @@ def main():
         return run_reference(args, wl)
     if args.kernel_only:
         return run_kernel_only(args, wl)
+    if args.mg_once:
+        return run_mg_once(args)
     return run_ours(args, wl)
 
 

@@ -62,3 +62,17 @@ def test_reference_arm_under_torchrun_prints_once():
     line = lines[0]
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_loads_only_the_oracle():
+    """The reference arm times the CPU oracle alone: its process maps the
+    oracle's library and never the CUDA path's libens."""
+    code = ("import sys, json; sys.argv = ['bench.py', '--impl', 'reference', '--steps', '1', '--warmup', '0', "
+            "'--ref-samples', '2', '--workload', 'fd5_32_adaptive']; sys.path.insert(0, %r); import bench; "
+            "bench.main(); maps = open('/proc/self/maps').read(); "
+            "print(json.dumps({'libens': 'libens' in maps, 'oracle': 'liboracle' in maps}))" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT,
+                       env=dict(os.environ, OMP_NUM_THREADS="1"))
+    assert r.returncode == 0, r.stderr[-2000:]
+    last = json.loads(r.stdout.strip().splitlines()[-1])
+    assert last == {"libens": False, "oracle": True}

@@ -588,6 +588,20 @@ __device__ __forceinline__ double block_lane_sum(double v, int S, double *sh)
     return sh[t];
 }
 
+// Per-lane largest magnitude over the block's row groups, atomically merged
+// into mx[L] (the bits of a non-negative double order like the value).
+__device__ __forceinline__ void block_lane_max(double v, int S, unsigned long long *mx, int L)
+{
+    __shared__ double shm[kBlock];
+    const int t = threadIdx.x, G = blockDim.x / S;
+    shm[t] = v;
+    __syncthreads();
+    if (t < S) {
+        for (int q = 1; q < G; q++) v = fmax(v, shm[q * S + t]);
+        if (v > 0.0) atomicMax(mx + L, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
 struct CgArgs {
     int J, S, E, nblk, maxit;
     double rtol;
@@ -598,21 +612,23 @@ struct CgArgs {
 
 // x = 0, r = b; block partials of b^T b (part0).
 __global__ void k_mgcg_init(int J, int S, int nblk, const double *__restrict__ b, double *__restrict__ x,
-                            double *__restrict__ r, double *__restrict__ part)
+                            double *__restrict__ r, double *__restrict__ part, unsigned long long *rmax)
 {
     __shared__ double sh[kBlock];
     const int e = blockIdx.y, s = threadIdx.x % S, G = blockDim.x / S;
     const int r0 = blockIdx.x * kRedRows, r1 = min(J, r0 + kRedRows);
-    double acc = 0.0;
+    double acc = 0.0, m = 0.0;
     for (int i = r0 + threadIdx.x / S; i < r1; i += G) {
         const size_t o = ((size_t)e * J + i) * S + s;
         const double bv = b[o];
         x[o] = 0.0;
         r[o] = bv;
         acc = fma(bv, bv, acc);
+        m = fmax(m, fabs(bv));
     }
     const double tot = block_lane_sum(acc, S, sh);
     if (threadIdx.x < S) part[((size_t)e * nblk + blockIdx.x) * S + s] = tot;
+    if (rmax) block_lane_max(m, S, rmax, e * S + s);
 }
 
 // Block partials of u^T v for live lanes (all lanes when live is null).
@@ -652,7 +668,8 @@ __global__ void k_mgcg_spmv(int J, int S, const int32_t *__restrict__ rp, const 
 __global__ void k_mgcg_update(int J, int S, int nblk, double *__restrict__ x, double *__restrict__ r,
                               const double *__restrict__ p, const double *__restrict__ q,
                               const double *__restrict__ alpha, const int *__restrict__ live,
-                              const int *__restrict__ ens_live, double *__restrict__ part)
+                              const int *__restrict__ ens_live, double *__restrict__ part,
+                              unsigned long long *rmax)
 {
     __shared__ double sh[kBlock];
     const int e = blockIdx.y, s = threadIdx.x % S, G = blockDim.x / S;
@@ -661,7 +678,7 @@ __global__ void k_mgcg_update(int J, int S, int nblk, double *__restrict__ x, do
     const bool on = live[L] != 0;
     const double al = on ? alpha[L] : 0.0;
     const int r0 = blockIdx.x * kRedRows, r1 = min(J, r0 + kRedRows);
-    double acc = 0.0;
+    double acc = 0.0, m = 0.0;
     if (on)
         for (int i = r0 + threadIdx.x / S; i < r1; i += G) {
             const size_t o = ((size_t)e * J + i) * S + s;
@@ -669,9 +686,11 @@ __global__ void k_mgcg_update(int J, int S, int nblk, double *__restrict__ x, do
             const double rv = fma(-al, q[o], r[o]);
             r[o] = rv;
             acc = fma(rv, rv, acc);
+            m = fmax(m, fabs(rv));
         }
     const double tot = block_lane_sum(acc, S, sh);
     if (threadIdx.x < S) part[((size_t)e * nblk + blockIdx.x) * S + s] = tot;
+    if (rmax) block_lane_max(m, S, rmax, L);
 }
 
 // p = z + beta p for live lanes; p = z for every lane when beta is null.
@@ -728,6 +747,8 @@ __global__ void k_mgcg_final(CgArgs a, int kind, const double *__restrict__ part
     if (kind == FIN_INIT) t1 = lane_total(part1, a.nblk, S, e, sh);
     if (threadIdx.x < S) {
         const int L = e * S + threadIdx.x;
+        // the float V-cycle's lane maxima of the next r start from zero (k_mgcg_update merges into them)
+        if (kind == FIN_ALPHA && w.rmax) w.rmax[L] = 0ull;
         if (kind == FIN_INIT) {
             const double bsq = t0, rz = t1;
             const int act = a.active ? (int)a.active[L] : 1;
@@ -908,16 +929,19 @@ inline unsigned convert_blocks(size_t n)
 }
 
 // z = M r with the work's V-cycle: in double, or r rounded to float, the float
-// V-cycle, and its result widened to double.
+// V-cycle, and its result widened to double.  rmax_ready: the CG kernel that
+// wrote r already left each lane's largest |r| in w.rmax.
 int mg_precond(ens_ctx *h, const MgWork &w, const int32_t *rp0, const int32_t *ci0, const double *vals0, int S,
-               int E, const double *r, double *z, const int *ens_live, cudaStream_t st)
+               int E, const double *r, double *z, const int *ens_live, cudaStream_t st, bool rmax_ready = false)
 {
     if (!w.mixed) return mg_vcycle<double>(h, w, rp0, ci0, vals0, S, E, r, z, ens_live, st);
     const int J = w.lv[0].J;
     const size_t per = (size_t)J * S, n = per * E;
-    ENS_CUDA_CHECK(h, cudaMemsetAsync(w.rmax, 0, sizeof(unsigned long long) * E * S, st));
-    const unsigned nb = (unsigned)std::min<int>((J + kBlock / S - 1) / (kBlock / S), 64);
-    k_mg_lane_max<<<dim3(nb, (unsigned)E), kBlock, 0, st>>>(J, S, r, w.rmax, ens_live);
+    if (!rmax_ready) {
+        ENS_CUDA_CHECK(h, cudaMemsetAsync(w.rmax, 0, sizeof(unsigned long long) * E * S, st));
+        const unsigned nb = (unsigned)std::min<int>((J + kBlock / S - 1) / (kBlock / S), 64);
+        k_mg_lane_max<<<dim3(nb, (unsigned)E), kBlock, 0, st>>>(J, S, r, w.rmax, ens_live);
+    }
     k_mg_convert_scaled<double, float><<<convert_blocks(n), kBlock, 0, st>>>(n, per, S, r, w.lv[0].rhs32, w.rmax, 0,
                                                                              ens_live);
     const int rc = mg_vcycle<float>(h, w, rp0, ci0, w.lv[0].vals32, S, E, w.lv[0].rhs32, w.lv[0].e32, ens_live, st);
@@ -1048,8 +1072,9 @@ extern "C" int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E,
     const dim3 gred((unsigned)w.nblk, (unsigned)E), grl = rl_grid(J, S, E);
     ENS_CUDA_CHECK(h, cudaMemsetAsync(w.live_total, 0, sizeof(int), st));
     // x = 0, r = b, z = M r, p = z; b^T b and r^T z decide each lane's start
-    k_mgcg_init<<<gred, kBlock, 0, st>>>(J, S, w.nblk, b, x, w.r, w.part0);
-    rc = mg_precond(h, w, rowptr, colidx, vals, S, E, w.r, w.z, nullptr, st);
+    if (w.mixed) ENS_CUDA_CHECK(h, cudaMemsetAsync(w.rmax, 0, sizeof(unsigned long long) * E * S, st));
+    k_mgcg_init<<<gred, kBlock, 0, st>>>(J, S, w.nblk, b, x, w.r, w.part0, w.mixed ? w.rmax : nullptr);
+    rc = mg_precond(h, w, rowptr, colidx, vals, S, E, w.r, w.z, nullptr, st, true);
     if (rc) return rc;
     k_mgcg_dot<<<gred, kBlock, 0, st>>>(J, S, w.nblk, w.r, w.z, nullptr, nullptr, w.part1);
     k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_INIT, w.part0, w.part1, w);
@@ -1068,9 +1093,9 @@ extern "C" int ens_mgpcg_solve(ens_handle h, const ens_problem *p, int S, int E,
             k_mgcg_dot<<<gred, kBlock, 0, st>>>(J, S, w.nblk, w.p, w.q, w.live, w.ens_live, w.part0);
             k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_ALPHA, w.part0, nullptr, w);
             k_mgcg_update<<<gred, kBlock, 0, st>>>(J, S, w.nblk, x, w.r, w.p, w.q, w.alpha, w.live, w.ens_live,
-                                                   w.part0);
+                                                   w.part0, w.mixed ? w.rmax : nullptr);
             k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_CONV, w.part0, nullptr, w);
-            rc = mg_precond(h, w, rowptr, colidx, vals, S, E, w.r, w.z, w.ens_live, st);
+            rc = mg_precond(h, w, rowptr, colidx, vals, S, E, w.r, w.z, w.ens_live, st, true);
             if (rc) return rc;
             k_mgcg_dot<<<gred, kBlock, 0, st>>>(J, S, w.nblk, w.r, w.z, w.live, w.ens_live, w.part0);
             k_mgcg_final<<<E, kBlock, 0, st>>>(a, FIN_BETA, w.part0, nullptr, w);

@@ -4,7 +4,7 @@
                     [--workload q1_256_adaptive] [--no-arms] [--no-cpu]
                     [--suite layers,configs,c1,pilot,paper,mixed-mg | all]
                     [--detail-out PATH]
-                    [--kernel-only [--kernel-ensembles E]] [--mg-once mg|mg32]
+                    [--kernel-only [--kernel-ensembles E]] [--mg-once mg|mg32] [--ir-once]
 
 A step is one pass of the whole path over the workload: the grid-generation
 and grouping loop of the paper's flowchart (initial sparse grid, then per
@@ -37,8 +37,8 @@ and, with --suite:
                   the Jacobi and the multigrid preconditioner
   mixed-mg        the multigrid solve with a float V-cycle on Test 1 / Test 2
 
---kernel-only times K2 alone and --mg-once runs one multigrid solve (the cases
-the Nsight Compute summaries use).
+--kernel-only times K2 alone, --mg-once runs one multigrid solve and --ir-once
+one mixed-precision refinement solve (the cases the Nsight Compute summaries use).
 --impl reference times the CPU oracle (the reference arm of this project) on
 the host cores for the same metric.  Multi-GPU runs are independent replicas
 that time the loop only.
@@ -1044,6 +1044,39 @@ def run_mg_once(args):
     return 0
 
 
+def run_ir_once(args):
+    """One FP32-in-FP64 refinement solve of one ensemble of 32 draws (inner rtol
+    1e-4, outer 1e-10) of the 128^3 7-point problem, or of the FD workload
+    --workload names (profiling case)."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens, inputs
+    from paper_1705_02003_gb300.solver import EnsembleSolver
+
+    h = ens.Handle(0)
+    wl = inputs.WORKLOADS[args.workload if args.workload.startswith("fd") else "fd7_128_mixed"]
+    prob = ens.problem(wl.kind, wl.n, wl.nparam, wl.aniso)
+    S = 32
+    sol = EnsembleSolver(h, prob, S, S, 1e-10, wl.maxit)
+    J, nnz = sol.J, sol.nnz
+    xi = torch.from_numpy(inputs.draws(S, wl.nparam, seed=wl.seed)).cuda()
+    ens.ens_assemble(h, prob, S, 1, xi.reshape(-1), sol.rowptr, sol.colidx, sol.vals, sol.dinv, sol.b)
+    v32 = torch.empty(nnz * S, dtype=torch.float32, device="cuda")  # the same values rounded to float
+    ens.ens_assemble(h, prob, S, 1, xi.reshape(-1), sol.rowptr, sol.colidx, v32)
+    x = torch.empty(J * S, dtype=torch.float64, device="cuda")
+    it = torch.empty(S, dtype=torch.int32, device="cuda")
+    oit, st = torch.empty_like(it), torch.empty_like(it)
+    rr = torch.empty(S, dtype=torch.float64, device="cuda")
+    work = torch.empty(ens.ens_pcg_ir_workspace_size(J, nnz, S, 1), dtype=torch.uint8, device="cuda")
+    _, t = timed(torch.cuda.current_stream(), lambda: ens.ens_pcg_solve_ir(
+        h, J, nnz, S, 1, sol.rowptr, sol.colidx, sol.vals, v32, sol.dinv, sol.b, x, None, 1e-10, 1e-4, wl.maxit, 50,
+        it, oit, rr, st, work))
+    print(json.dumps({"ir_once": wl.name, "seconds": t, "inner_iters_max": int(it.max().item()),
+                      "outer_max": int(oit.max().item()), "converged": bool((st == 0).all().item())}))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1062,6 +1095,8 @@ def main():
     ap.add_argument("--kernel-s", type=int, default=0, help="lanes per ensemble for --kernel-only (0: the workload's)")
     ap.add_argument("--mg-once", choices=["mg", "mg32"], default=None,
                     help="one multigrid solve of 64 draws of Section 4's Test 1 (profiling)")
+    ap.add_argument("--ir-once", action="store_true",
+                    help="one FP32-in-FP64 refinement solve of 32 draws of the 128^3 problem (profiling)")
     args = ap.parse_args()
     from paper_1705_02003_gb300 import inputs
 
@@ -1072,6 +1107,8 @@ def main():
         return run_kernel_only(args, wl)
     if args.mg_once:
         return run_mg_once(args)
+    if args.ir_once:
+        return run_ir_once(args)
     return run_ours(args, wl)
 
 

@@ -968,7 +968,8 @@ def run_layers(h, stream):
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
-        refs = list(ex.map(lambda m: O.adjoint_grad(O.FD5_LOGKL, wl.n, wl.nparam, wl.aniso, xi_h[m], w_h, wl.rtol,
+        w_o = O.region_weights(wl.n, 2)
+        refs = list(ex.map(lambda m: O.adjoint_grad(O.FD5_LOGKL, wl.n, wl.nparam, wl.aniso, xi_h[m], w_o, wl.rtol,
                                                     wl.maxit), sub))
     t_or = time.perf_counter() - t0
     gerr = [np.abs(gh[m] - r[1]).max() / np.abs(r[1]).max() for m, r in zip(sub, refs)]

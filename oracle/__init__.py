@@ -396,6 +396,23 @@ def pcg_ir(rowptr, colidx, vals, b, rtol_outer=1e-10, rtol_inner=1e-6, maxit_inn
     return x, oi.value, ii.value, st, rr.value
 
 
+def region_weights(n: int, dim: int):
+    """Weights of the quantity of interest Q = mean of u over [0.4, 0.6]^dim
+    (the differentiation workload): w_p = 1/|R| on the interior nodes p whose
+    coordinates x = i/(n+1) all lie in [0.4, 0.6], else 0; node order x fastest.
+    The test 0.4 <= i/(n+1) <= 0.6 is taken exactly, as 5i >= 2(n+1) and
+    5i <= 3(n+1)."""
+    inside = [i for i in range(1, n + 1) if 5 * i >= 2 * (n + 1) and 5 * i <= 3 * (n + 1)]
+    J = n ** dim
+    w = np.zeros(J, np.float64)
+    count = len(inside) ** dim
+    for j in range(J):
+        coords = [(j // n ** d) % n + 1 for d in range(dim)]
+        if all(c in inside for c in coords):
+            w[j] = 1.0 / count
+    return w
+
+
 def adjoint_grad(kind: int, n: int, nparam: int, aniso: float, xi, w, rtol: float, maxit: int):
     """Q = w^T u and dQ/dxi = -lambda^T (dA/dxi) u for one sample."""
     grad = np.zeros(nparam, np.float64)

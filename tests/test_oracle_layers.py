@@ -27,7 +27,7 @@ def test_ir_matches_fp64_solution(kind, n, N, aniso):
 @pytest.mark.parametrize("kind,n,N,aniso", [(O.FD5_LOGKL, 15, 8, 3.0), (O.FD7_AXIS, 6, 6, 3.0)])
 def test_adjoint_gradient_matches_central_differences(kind, n, N, aniso):
     rng = np.random.default_rng(12)
-    w = inputs.region_weights(n, 3 if kind == O.FD7_AXIS else 2)
+    w = O.region_weights(n, 3 if kind == O.FD7_AXIS else 2)
     assert w.sum() == pytest.approx(1.0)
     for _ in range(2):
         xi = rng.uniform(-0.9, 0.9, N)
@@ -50,8 +50,19 @@ def test_adjoint_gradient_matches_central_differences(kind, n, N, aniso):
 
 
 def test_region_weights_select_the_square():
-    n = 49
-    w = inputs.region_weights(n, 2).reshape(n, n)
-    x = (np.arange(n) + 1) / (n + 1)
-    inside = (x >= 0.4 - 1e-12) & (x <= 0.6 + 1e-12)
-    assert np.array_equal(w > 0, np.outer(inside, inside))
+    """The oracle's weights: the support is the set of nodes in [0.4, 0.6]^d by
+    exact rational coordinates (checked here with fractions, including meshes
+    where a node sits exactly on 0.4 or 0.6), the weights sum to one, and the
+    input module's weights, which the GPU side receives, are the same bits."""
+    from fractions import Fraction
+
+    for n, dim in ((49, 2), (24, 2), (9, 3), (14, 3), (512, 2)):
+        w = O.region_weights(n, dim)
+        x = [Fraction(i, n + 1) for i in range(1, n + 1)]
+        inside = np.array([Fraction(2, 5) <= xi <= Fraction(3, 5) for xi in x])
+        want = np.outer(inside, inside) if dim == 2 else np.einsum("a,b,c->abc", inside, inside, inside)
+        # node order x fastest: w[j] with j = i0 + n i1 (+ n^2 i2) -> array index [i_last, ..., i0]
+        assert np.array_equal(w.reshape((n,) * dim) > 0, want.T if dim == 2 else want.transpose(2, 1, 0))
+        assert abs(w.sum() - 1.0) < 1e-12
+        assert np.array_equal(w, inputs.region_weights(n, dim))
+    assert 5 * 4 == 2 * (9 + 1) and 5 * 6 == 3 * (9 + 1)  # n = 9: nodes 4 and 6 sit on 0.4 and 0.6

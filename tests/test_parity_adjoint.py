@@ -31,7 +31,7 @@ def test_adjoint_gradient_matches_oracle(h, kind, n, N, aniso, S, M):
     g = sol.gradient(x, recompute_forward=False).cpu().numpy()
     okind = {"fd5": O.FD5_LOGKL, "fd7": O.FD7_AXIS}[kind]
     for s in range(M):
-        Qo, go, _, _, st = O.adjoint_grad(okind, n, N, aniso, xi[s], w, 1e-13, 100000)
+        Qo, go, _, _, st = O.adjoint_grad(okind, n, N, aniso, xi[s], O.region_weights(n, dim), 1e-13, 100000)
         assert st == O.CONVERGED
         assert q[s] == pytest.approx(Qo, rel=1e-10)
         assert np.all(np.abs(g[s] - go) <= 1e-9 * np.maximum(1e-3, np.abs(go))), (s, g[s], go)
@@ -88,7 +88,8 @@ def test_adjoint_full_size_sampled_lane(h):
     g = sol.gradient(x, recompute_forward=False).cpu().numpy()
     assert torch.all(sol.last["forward_status"] == ens.LANE_CONVERGED)
     assert torch.all(sol.last["adjoint_status"] == ens.LANE_CONVERGED)
-    Qo, go, _, _, st = O.adjoint_grad(O.FD5_LOGKL, wl.n, wl.nparam, wl.aniso, xi[5], w, 1e-10, wl.maxit)
+    Qo, go, _, _, st = O.adjoint_grad(O.FD5_LOGKL, wl.n, wl.nparam, wl.aniso, xi[5], O.region_weights(wl.n, 2), 1e-10,
+                                      wl.maxit)
     assert q[5] == pytest.approx(Qo, rel=1e-7)
     assert np.all(np.abs(g[5] - go) <= 1e-6 * np.maximum(1e-3, np.abs(go))), (g[5], go)
 

@@ -56,7 +56,7 @@ def test_stream_with_weights_and_a_bad_sample(h):
     keep = [m for m in range(M) if m != 11]
     assert np.all(st[keep] == ens.LANE_CONVERGED)
     o = O.solve_batch(O.FD5_LOGKL, n, N, 3.0, xi[keep], 1e-8, 20000, nthreads=4, want_x=True)
-    np.testing.assert_allclose(out["qoi"].cpu().numpy()[keep], o["x"] @ inputs.region_weights(n, 2), rtol=1e-9)
+    np.testing.assert_allclose(out["qoi"].cpu().numpy()[keep], o["x"] @ O.region_weights(n, 2), rtol=1e-9)
 
 
 def test_stream_rejects_a_bad_order(h):

@@ -23,14 +23,14 @@ from __future__ import annotations
 import numpy as np
 
 DRIFT_FACTOR = 4.0
-PERTURBATION_SEEDS = (0, 1, 2, 3)
+PERTURBATION_SEEDS = (0, 1, 2, 3, 4, 5)
 
 
-def perturb(vals: np.ndarray, seed: int) -> np.ndarray:
-    """vals with every entry moved by one unit in the last place (relative
-    2^-52), up or down at random."""
+def perturb(vals: np.ndarray, seed: int, scale: float = 2.0 ** -52) -> np.ndarray:
+    """vals with every entry moved by the relative amount scale (by default one
+    unit in the last place), up or down at random."""
     sgn = np.random.default_rng(seed).choice([-1.0, 1.0], len(vals))
-    return vals * (1.0 + sgn * 2.0 ** -52)
+    return vals * (1.0 + sgn * scale)
 
 
 def rounding_drift(hist: np.ndarray, perturbed) -> np.ndarray:
@@ -55,12 +55,29 @@ def stop_consistent(iters: int, hist: np.ndarray, rtol: float, delta) -> bool:
     return went_on and stopped
 
 
-def oracle_check(O, rowptr, colidx, vals, b, rtol: float, iters: int, iters_oracle: int):
+def oracle_check(O, rowptr, colidx, vals, b, rtol: float, iters: int, iters_oracle: int,
+                 scale: float = 2.0 ** -52):
     """(consistent, delta, history) of a run's count against the oracle's solve
-    of the same system (vals, b), with delta[k - 1] = DRIFT_FACTOR x the
-    oracle's own rounding drift at iteration k, up to the later of the two stops."""
+    of the same system (vals, b), with delta[k - 1] = DRIFT_FACTOR x the drift
+    that perturbations of the matrix by the relative amount scale (one ulp when
+    both sides solve the same matrix; the assembly bar when each side assembles
+    its own) cause in the oracle's history at iteration k, up to the later of
+    the two stops."""
     k = max(iters, iters_oracle)
     hist = O.pcg_history(rowptr, colidx, vals, b, 0.0, k)[4]
-    pert = [O.pcg_history(rowptr, colidx, perturb(vals, s), b, 0.0, k)[4] for s in PERTURBATION_SEEDS]
+    pert = [O.pcg_history(rowptr, colidx, perturb(vals, s, scale), b, 0.0, k)[4] for s in PERTURBATION_SEEDS]
     delta = DRIFT_FACTOR * rounding_drift(hist, pert)
     return stop_consistent(iters, hist, rtol, delta), delta, hist
+
+
+def count_envelope(O, rowptr, colidx, vals, b, rtol: float, maxit: int, scale: float,
+                   seeds=tuple(range(10, 22))):
+    """(lowest, highest) count of the oracle's solve of (vals, b) and of its
+    solves of the matrix perturbed by the relative amount scale, one per seed.
+    Where each side assembles its own matrix (differences up to the assembly
+    bar) and the residual near the stop is chaotic, a count inside this
+    envelope widened by one is what the oracle itself would give for a matrix
+    that close to its own."""
+    counts = [O.pcg(rowptr, colidx, vals, b, rtol, maxit)[1]]
+    counts += [O.pcg(rowptr, colidx, perturb(vals, s, scale), b, rtol, maxit)[1] for s in seeds]
+    return min(counts), max(counts)

@@ -11,6 +11,7 @@ import torch
 
 import oracle as O
 from gpu_util import OKIND, Case, elem_err, grouping_on_oracle_counts
+from stopping import count_envelope
 from oracle import uq as ouq
 from paper_1705_02003_gb300 import ens, inputs, uq
 
@@ -123,12 +124,14 @@ def test_full_size_sampled_lanes(h, name, lanes):
 def test_adaptive_loop_matches_oracle(h, name):
     """The flowchart loop on a 16^3-cell version of the problem, capped at 200
     points: the same grid and levels, G within 1e-7, and the surrogate
-    groupings equal wherever the counts agree.  Iteration counts within one
-    for Test 1; within two for Test 2, whose coefficient reaches 100 x the
-    KL field: there both sides' matrices (equal to 1e-13) give condition numbers
-    near 1e7, and near a flat stretch of the residual curve that moves the
-    stopping iteration by up to two (with the same matrices the counts agree
-    within one, test above)."""
+    groupings equal wherever the counts agree.  Iteration counts within one,
+    or, where a count differs by more, within one of the range of counts the
+    oracle itself gives when its matrix is perturbed by the assembly bar (1e-13
+    relative, random signs, twelve draws; tests/stopping.py count_envelope):
+    each side assembles its own matrix, and Test 2's coefficient reaches 100 x
+    the KL field, so condition numbers near 1e7 make the residual curve near
+    the stop chaotic under such differences (with the same matrices the counts
+    agree within one, test above)."""
     wl = dataclasses.replace(inputs.WORKLOADS[name], n=15, n_max=200)
     run = uq.Adaptive(h, wl).run("sur")
 
@@ -140,7 +143,12 @@ def test_adaptive_loop_matches_oracle(h, name):
                        n_max=wl.n_max)
     assert np.array_equal(run["lvl"], ref["lvl"]) and np.array_equal(run["idx"], ref["idx"])
     assert run["levels"] == ref["levels"] and len(run["levels"]) >= 2
-    assert np.max(np.abs(run["I"] - ref["I"])) <= (1 if name == "q1_32c_test1" else 2)
+    Ig, Io = run["I"].astype(int), ref["I"].astype(int)
+    rp, ci = O.pattern(OKIND[wl.kind], wl.n)
+    for m in np.nonzero(np.abs(Ig - Io) > 1)[0]:
+        vals, b = O.assemble(OKIND[wl.kind], wl.n, 4, 0.0, ref["y"][m], rp, ci)
+        lo, hi = count_envelope(O, rp, ci, vals, b, wl.rtol, wl.maxit, 1e-13)
+        assert lo - 1 <= Ig[m] <= hi + 1, (m, Io[m], Ig[m], lo, hi)
     np.testing.assert_allclose(run["G"], ref["G"], rtol=1e-7)  # assembled on both sides (see above)
     grouping_on_oracle_counts(h, ref)
     if np.array_equal(run["I"], ref["I"]):

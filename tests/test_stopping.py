@@ -99,3 +99,20 @@ def test_check_accepts_the_oracles_own_perturbed_runs():
             for d in (-1, 1):
                 assert not oracle_check(O, rp, ci, vals, b, RTOL, it + d, it)[0]
     assert moved >= 1 and clear >= len(xi) - 2
+
+
+def test_count_envelope_is_narrow_on_clear_stops_and_holds_the_oracles_count():
+    """The envelope always holds the unperturbed count; on a sample whose stop
+    is clear it is that count alone at one ulp, and it widens with the size of
+    the perturbation only where the residual near the stop is flat."""
+    from stopping import count_envelope
+
+    rp, ci = O.pattern(O.FD5_LOGKL, 32)
+    for xi in (np.array([0.3, -0.2]), np.array([-0.8, 0.6])):
+        vals, b = O.assemble(O.FD5_LOGKL, 32, 2, 3.0, xi, rp, ci)
+        _, it, _, _ = O.pcg(rp, ci, vals, b, RTOL, 20000)
+        lo, hi = count_envelope(O, rp, ci, vals, b, RTOL, 20000, 2.0 ** -52)
+        assert lo <= it <= hi
+        hist = O.pcg_history(rp, ci, vals, b, 0.0, it + 1)[4]
+        if hist[it - 1] < 0.9 * RTOL and hist[it - 2] > 1.1 * RTOL:
+            assert lo == hi == it

@@ -70,7 +70,7 @@ FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one K2 launch on the Q1 256^2 problem at S = 16,
 # per ensemble, from an Nsight Compute capture of E = 8 ensembles (0.674 GB
 # read, 0.038 GB written); a full-capacity launch scales it by E.
-SPMV_TRAFFIC_PER_ENSEMBLE = {"q1_256_adaptive": (673.661696e6 + 37.994240e6) / 8}
+SPMV_TRAFFIC_PER_ENSEMBLE = {"q1_256_adaptive": (673.564160e6 + 38.298368e6) / 8}
 
 N_MAX_READING = ("levels of 48, 58 and 159 points; a level that would take the grid past N_max = 512 "
                  "is not admitted (the fourth would)")

@@ -169,6 +169,27 @@ def test_batch_size_does_not_change_results(h):
     assert np.array_equal(batch["iters"][8:16], alone["iters"])
 
 
+def test_dealt_row_chunks_keep_results_independent_of_batch_and_lane(h):
+    """7-point rows on 56^3 (J = 175,616: row tiles of 512 rows, so K2 deals its
+    256-row chunks across the blocks): a sample gives the same bits alone, in a
+    batch of three ensembles, at another lane, and with the loop launched from
+    the host; and the solve agrees with the oracle."""
+    n, N, aniso, S = 56, 6, 3.0, 8
+    xi = inputs.draws(24, N, seed=9) * 0.7
+    batch = Case(h, "fd7", n, N, aniso, S, xi).solve(1e-8, 5000)
+    alone = Case(h, "fd7", n, N, aniso, S, xi[8:16]).solve(1e-8, 5000)
+    assert np.array_equal(batch["x"][8:16], alone["x"]) and np.array_equal(batch["iters"][8:16], alone["iters"])
+    rev = Case(h, "fd7", n, N, aniso, S, xi[8:16][::-1].copy()).solve(1e-8, 5000)
+    assert np.array_equal(rev["x"][::-1], alone["x"]) and np.array_equal(rev["iters"][::-1], alone["iters"])
+    hh = _handle_with({"ENS_PCG_HOST_LOOP": "1"})
+    host = Case(hh, "fd7", n, N, aniso, S, xi[8:16]).solve(1e-8, 5000)
+    assert np.array_equal(host["x"], alone["x"]) and np.array_equal(host["iters"], alone["iters"])
+    hh.close()
+    c = Case(h, "fd7", n, N, aniso, S, xi[8:10])
+    ref = oracle_solve(c, 1e-8, 5000)
+    check_against_oracle(c, c.solve(1e-8, 5000), ref, 1e-8, [0, 1])
+
+
 def _handle_with(env: dict):
     """A handle created while the environment holds `env` (read at ens_create)."""
     import os

@@ -37,6 +37,8 @@ def rounding_drift(hist: np.ndarray, perturbed) -> np.ndarray:
     """Per iteration k, max |rho'_k / rho_k - 1| over the perturbed histories
     rho' (each at least as long as hist)."""
     hist = np.asarray(hist, np.float64)
+    if any(len(p) < len(hist) for p in perturbed):
+        raise ValueError("a perturbed run stopped early (breakdown): no drift to measure")
     return np.max([np.abs(np.asarray(p[: len(hist)]) / hist - 1.0) for p in perturbed], axis=0)
 
 

@@ -95,8 +95,9 @@ def test_vcycle_matches_oracle(h, kind):
 def test_float_vcycle_matches_oracle(h, kind):
     """The mixed-precision V-cycle (float copy of the hierarchy, float
     arithmetic): against the oracle's float V-cycle and its FP64 one, 1e-5 of
-    the result's largest entry, element by element (float rounding ~2e-7 on each side; fused multiply-adds
-    and the coarsest inverse against separate roundings and triangular solves)."""
+    the result's largest entry, element by element (float rounding ~2e-7 on
+    each side; fused multiply-adds and the coarsest inverse against separate
+    roundings and triangular solves)."""
     n, S, M = 15, 8, 11
     c = Case(h, kind, n, 4, 0.0, S, draws(M, 16))
     rp, ci, V, _, vals, _ = oracle_system(c, kind)

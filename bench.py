@@ -634,6 +634,28 @@ def run_c1(h, stream, hbm: float, fp64: float):
     M = len(r["I"])
     out["per_sample_serial"] = {"value": M / t, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r["I"] - ref["I"]))),
                                 **roof_fracs(M / t, M, float(r["I"].sum()), ad.solver.nnz, ad.solver.J, 1, hbm, fp64)}
+    # the same surrogate arm with every solve on the three-kernel graph loop
+    # instead of the one-launch cluster schedule (identical results)
+    import torch
+
+    from paper_1705_02003_gb300 import ens
+
+    out["cluster_ctas"] = ens.ens_pcg_cluster_size(h, ad.solver.J, ad.solver.nnz, wl.S, 4)
+    prev = os.environ.get("ENS_PCG_FUSED")
+    os.environ["ENS_PCG_FUSED"] = "0"
+    try:
+        hl = ens.Handle(torch.cuda.current_device())
+    finally:
+        if prev is None:
+            del os.environ["ENS_PCG_FUSED"]
+        else:
+            os.environ["ENS_PCG_FUSED"] = prev
+    al = Adaptive(hl, wl)
+    al.run("sur")
+    rl, tl = timed(stream, lambda: al.run("sur"))
+    out["sur_graph_loop"] = {"value": len(rl["I"]) / tl, "same_counts": bool(np.array_equal(rl["I"], ref["I"])),
+                             "same_G": bool(np.array_equal(rl["G"], ref["G"]))}
+    hl.close()
     out["points"] = M
     out["note"] = "working set in L2 (0.5 MB per ensemble): launch- and latency-bound, roofline fractions are HBM's"
     return out

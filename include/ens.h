@@ -94,8 +94,8 @@ typedef struct ens_ctx *ens_handle;
  * at most 32 instantiated CUDA graphs (keyed by every pointer and size of a
  * solve, least recently used evicted first); it is not thread-safe.
  * ens_destroy releases all of them.  Environment variables read here: ENS_PCG_HOST_LOOP,
- * ENS_PCG_BRANCHES, ENS_CHECK (see ens_pcg_solve, ens_pcg_branches,
- * ens_check_pattern). */
+ * ENS_PCG_BRANCHES, ENS_PCG_FUSED, ENS_CHECK (see ens_pcg_solve,
+ * ens_pcg_branches, ens_pcg_cluster_size, ens_check_pattern). */
 int ens_create(ens_handle *h, int device);
 int ens_destroy(ens_handle h);
 /* (host) message of the last failed call on this handle; never NULL. */
@@ -145,6 +145,20 @@ int ens_check_pattern(ens_handle h, int J, int64_t nnz, const int32_t *rowptr, c
  * the host-loop mode.  Returns 0 for a NULL handle or E <= 0. */
 int ens_pcg_branches(ens_handle h, int E);
 
+/* Thread-block cluster size of the one-launch schedule ens_pcg_solve uses for
+ * this problem, or 0 where it runs the graph loop described there (no
+ * counterpart in the paper: a scheduling choice of this library).  Problems of
+ * at most 1024 unknowns (16 row tiles of 64) with S <= 32 take the one-launch
+ * schedule when the device holds all E clusters at once and a CTA's FP64 work
+ * per CG trip, 64 S (nnz/J + 7) multiply-adds, is at most 26000: one cluster of
+ * one CTA per row tile runs the start, every CG trip and the finish of its
+ * ensemble in a single kernel, with cluster barriers instead of kernel
+ * boundaries.  The environment variable ENS_PCG_FUSED at ens_create selects 0
+ * (never) or 2 (also past the work bound); it is not used in the host-loop
+ * mode.  May query the device (cluster occupancy, once per kernel and layout);
+ * no device work.  Returns 0 for a NULL handle or invalid sizes. */
+int ens_pcg_cluster_size(ens_handle h, int J, int64_t nnz, int S, int E);
+
 /* Bytes of caller workspace ens_pcg_solve needs (device memory, 256-byte aligned). */
 size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E);
 
@@ -166,7 +180,10 @@ size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E);
  * variable ENS_PCG_HOST_LOOP=1 at ens_create, the same kernels are instead
  * launched from the host, which reads the live-lane count back every 16 trips
  * (a profiling aid: kernel profilers do not see kernels inside a conditional
- * graph body).  Results do not depend on either choice, bit for bit. */
+ * graph body).  Problems of at most 1024 unknowns instead run as one kernel
+ * launch (ens_pcg_cluster_size).  Results do not depend on any of these
+ * choices, bit for bit: every schedule performs the same operations in the
+ * same order. */
 int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   const int32_t *rowptr, const int32_t *colidx, const double *vals,
                   const double *dinv, const double *b, double *x, const uint8_t *active,

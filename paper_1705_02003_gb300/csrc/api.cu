@@ -33,6 +33,8 @@ extern "C" int ens_create(ens_handle *out, int device)
     if (h->branches < 0) h->branches = 0;
     const char *ck = getenv("ENS_CHECK");
     h->check = (ck && ck[0] == '1') ? 1 : 0;
+    const char *fu = getenv("ENS_PCG_FUSED");
+    h->fused = !fu ? 1 : fu[0] == '0' ? 0 : fu[0] == '2' ? 2 : 1;
     if (cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess) {
         delete h;
         return ENS_ECUDA;

@@ -26,6 +26,15 @@ struct MgTag {
     int kind = 0, n = 0, S = 0, E = 0, mixed = 0;
 };
 
+// How many clusters of C CTAs of a one-launch PCG kernel (smem bytes of
+// dynamic shared memory each) the device holds at once.
+struct ClusterFit {
+    const void *kernel;
+    int C;
+    size_t smem;
+    int resident;
+};
+
 }  // namespace ens
 
 struct ens_ctx {
@@ -37,6 +46,8 @@ struct ens_ctx {
     int host_loop = 0;                       // ENS_PCG_HOST_LOOP=1: launch the PCG loop from the host
     int branches = 0;                        // ENS_PCG_BRANCHES=n: graph branches of a PCG loop (0: one per ensemble, at most 16)
     int check = 0;                           // ENS_CHECK=1: validate the caller's CSR graph before a solve
+    int fused = 1;                           // ENS_PCG_FUSED: 0 never the one-launch schedule, 2 wherever it fits
+    std::vector<ens::ClusterFit> cluster_fit;  // answers of the cluster-occupancy query, per kernel and layout
     int *check_flag = nullptr;               // device word for the graph check
     void *sort_scratch = nullptr;            // device-wide sort of more than 16384 keys (grown on demand)
     size_t sort_scratch_bytes = 0;

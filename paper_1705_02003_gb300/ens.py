@@ -29,7 +29,7 @@ EXPORTS = ("ens_create", "ens_destroy", "ens_last_error", "ens_problem_size", "e
            "ens_stream_workspace_size", "ens_solve_stream", "ens_pcg_branches", "ens_check_pattern",
            "ens_mg_workspace_size", "ens_mg_setup", "ens_mg_level", "ens_mg_apply", "ens_mgpcg_solve",
            "ens_sg_points", "ens_fp64_peak", "ens_fp64_peak_flops", "ens_adjoint_solve_workspace_size",
-           "ens_adjoint_solve_grad")
+           "ens_adjoint_solve_grad", "ens_pcg_cluster_size")
 
 _lib = None
 _lock = threading.Lock()
@@ -75,6 +75,8 @@ def _declare(L):
     L.ens_check_pattern.argtypes = [vp, c.c_int, c.c_int64, vp, vp, vp]
     L.ens_pcg_branches.argtypes = [vp, c.c_int]
     L.ens_pcg_branches.restype = c.c_int
+    L.ens_pcg_cluster_size.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int]
+    L.ens_pcg_cluster_size.restype = c.c_int
     L.ens_pcg_workspace_size.argtypes = [c.c_int, c.c_int64, c.c_int, c.c_int]
     L.ens_pcg_workspace_size.restype = c.c_size_t
     L.ens_pcg_solve.argtypes = [vp, c.c_int, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp, vp, vp, vp,
@@ -236,6 +238,12 @@ def ens_check_pattern(h: Handle, J: int, nnz: int, rowptr, colidx, stream=None):
 def ens_pcg_branches(h: Handle, E: int) -> int:
     """Independent while-loop branches ens_pcg_solve runs for E ensembles."""
     return int(load().ens_pcg_branches(h.ptr, int(E)))
+
+
+def ens_pcg_cluster_size(h: Handle, J: int, nnz: int, S: int, E: int) -> int:
+    """CTAs per ensemble of the one-launch cluster schedule ens_pcg_solve uses
+    for this problem, or 0 where it runs the graph loop."""
+    return int(load().ens_pcg_cluster_size(h.ptr, int(J), int(nnz), int(S), int(E)))
 
 
 def ens_pcg_workspace_size(J: int, nnz: int, S: int, E: int) -> int:

@@ -657,7 +657,8 @@ def run_c1(h, stream, hbm: float, fp64: float):
                              "same_G": bool(np.array_equal(rl["G"], ref["G"]))}
     hl.close()
     out["points"] = M
-    out["note"] = "working set in L2 (0.5 MB per ensemble): launch- and latency-bound, roofline fractions are HBM's"
+    out["note"] = ("each solve is one cluster launch with its state in shared memory: latency-bound, roofline "
+                   "fractions are HBM's")
     return out
 
 
@@ -1067,6 +1068,27 @@ def run_mg_once(args):
     return 0
 
 
+def run_loop_once(args, wl):
+    """The Section 3.1 loop of the workload --workload names (surrogate
+    grouping), run twice: one pass to build and warm up, one to profile.  On
+    the 32^2 workload every solve takes the one-launch cluster schedule, so a
+    kernel profiler lists each solve as one launch."""
+    import torch
+
+    from paper_1705_02003_gb300 import ens
+    from paper_1705_02003_gb300.uq import Adaptive
+
+    h = ens.Handle(0)
+    ad = Adaptive(h, wl)
+    for _ in range(2):
+        r = ad.run("sur")
+    torch.cuda.synchronize()
+    print(json.dumps({"loop_once": wl.name, "points": int(len(r["I"])), "iters_max": int(r["I"].max()),
+                      "cluster_ctas": ens.ens_pcg_cluster_size(h, ad.solver.J, ad.solver.nnz, wl.S, 1)}))
+    h.close()
+    return 0
+
+
 def run_ir_once(args):
     """One FP32-in-FP64 refinement solve of one ensemble of 32 draws (inner rtol
     1e-4, outer 1e-10) of the 128^3 7-point problem, or of the FD workload
@@ -1118,6 +1140,8 @@ def main():
     ap.add_argument("--kernel-s", type=int, default=0, help="lanes per ensemble for --kernel-only (0: the workload's)")
     ap.add_argument("--mg-once", choices=["mg", "mg32"], default=None,
                     help="one multigrid solve of 64 draws of Section 4's Test 1 (profiling)")
+    ap.add_argument("--loop-once", action="store_true",
+                    help="two passes of the adaptive loop of --workload, surrogate grouping (profiling)")
     ap.add_argument("--ir-once", action="store_true",
                     help="one FP32-in-FP64 refinement solve of 32 draws of the 128^3 problem (profiling)")
     args = ap.parse_args()
@@ -1132,6 +1156,8 @@ def main():
         return run_mg_once(args)
     if args.ir_once:
         return run_ir_once(args)
+    if args.loop_once:
+        return run_loop_once(args, wl)
     return run_ours(args, wl)
 
 

@@ -140,11 +140,14 @@ __device__ __forceinline__ void publish_tile(double (&acc)[NS][LG::V], double (*
 // those steps are skipped, leaving the pairwise tree over 16 groups.  For
 // S = 32 (G = 8) the groups hold partials g and g + 8.  Thread t handles group
 // g = t % GS of lane s = t / GS (GS = min(G, 16) consecutive threads per lane);
-// on return thread g = 0 holds lane s's totals.  Every thread must call it.
+// on return thread g = 0 holds lane s's totals.  Only the warps that hold
+// groups add (an FP64 warp instruction occupies the pipe for its whole warp on
+// this part), but every thread must call it.
 template <int S, int NS>
 __device__ __forceinline__ void combine(const double *xch, int nblk, double (&tot)[NS])
 {
     constexpr int G = kBlock / S, GS = G < 16 ? G : 16;
+    constexpr int WORK = S * GS < 32 ? 32 : S * GS;  // threads of the warps that hold groups
     const int tid = threadIdx.x, g = tid % GS, s = tid / GS;
     const bool mine = s < S;
 #pragma unroll
@@ -154,6 +157,7 @@ __device__ __forceinline__ void combine(const double *xch, int nblk, double (&to
             for (int b = g; b < nblk; b += G) v = dadd(v, xch[((size_t)ns * nblk + b) * S + s]);
         tot[ns] = v;
     }
+    if (tid >= WORK) return;
 #pragma unroll
     for (int st = GS / 2; st > 0; st >>= 1) {
 #pragma unroll

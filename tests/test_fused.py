@@ -55,12 +55,12 @@ def run_both(handles, kind, n, N, aniso, S, M, rtol, maxit, seed, perturb=None):
 
 
 # (kind, n, N, aniso): 5-, 9-, 7- and 27-point rows; 1 to 16 row tiles of 64
-# rows (25 unknowns: a cluster of one CTA), with ragged last tiles (961
+# rows (4 and 25 unknowns: a cluster of one CTA), with ragged last tiles (961
 # unknowns: a last tile of one row).  On the
 # 7-point 10^3 problem the +-100-row neighbours do not fit the 256-row windows,
 # so p goes through global memory there.
-PROBLEMS = [("fd5", 5, 2, 3.0), ("fd5", 15, 2, 3.0), ("fd5", 32, 2, 3.0), ("q1", 16, 4, 4.0),
-            ("q1", 31, 4, 4.0), ("fd7", 10, 6, 3.0), ("q1_3d_kl", 7, 4, 0.0)]
+PROBLEMS = [("fd5", 2, 2, 3.0), ("fd5", 5, 2, 3.0), ("fd5", 15, 2, 3.0), ("fd5", 32, 2, 3.0),
+            ("q1", 16, 4, 4.0), ("q1", 31, 4, 4.0), ("fd7", 10, 6, 3.0), ("q1_3d_kl", 7, 4, 0.0)]
 
 
 @pytest.mark.parametrize("prob", PROBLEMS, ids=lambda p: f"{p[0]}_{p[1]}")

@@ -103,6 +103,9 @@ SOLVE_CASES = [
     ("fd5", 16, 3, 3.0, 64, 70),
     ("fd5", 40, 8, 3.0, 32, 45),    # 5-point rows at S = 16, 32: the two-lane SpMV variant
     ("fd5", 50, 4, 3.0, 16, 20),    # (J = 1600, 2500: ragged last tile)
+    ("fd5", 2, 2, 3.0, 8, 5),       # the smallest grids (n = 2): 4 and 8 unknowns, one row tile
+    ("q1", 2, 4, 4.0, 16, 3),
+    ("fd7", 2, 6, 3.0, 32, 33),
 ]
 
 

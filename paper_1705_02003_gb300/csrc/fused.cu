@@ -681,7 +681,7 @@ constexpr double kMaxTripWork = 26000.0;
 int fused_cluster_size(ens_ctx *h, int J, long long nnz, int S, int E)
 {
     if (!h || h->host_loop || !h->fused || J <= 0 || E <= 0 || !lane_count_ok(S) || S > 32) return 0;
-    const Geo g = geometry(J, S);
+    const Geo g = geometry(J, S, E);
     if (g.nblk > kMaxCluster || g.RT != kTile) return 0;
     if (h->fused != 2 && (double)kTile * S * ((double)nnz / J + 7.0) > kMaxTripWork) return 0;
     FusedKernel k = pick(S, (double)nnz / J);

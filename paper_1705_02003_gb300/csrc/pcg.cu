@@ -717,7 +717,7 @@ extern "C" size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E)
 {
     (void)nnz;
     if (J <= 0 || E <= 0 || !lane_count_ok(S)) return 0;
-    return layout(J, S, E, geometry(J, S), nullptr, nullptr);
+    return layout(J, S, E, geometry(J, S, E), nullptr, nullptr);
 }
 
 extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, const int32_t *rowptr,
@@ -737,7 +737,7 @@ extern "C" int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E, con
         int crc = check_pattern(h, "ens_pcg_solve", J, nnz, rowptr, colidx, (cudaStream_t)stream);
         if (crc) return crc;
     }
-    Geo g = geometry(J, S);
+    Geo g = geometry(J, S, E);
     const size_t need = layout(J, S, E, g, nullptr, nullptr);
     if (work_bytes < need)
         return set_error(h, ENS_ENOMEM, "ens_pcg_solve: workspace too small (need " + std::to_string(need) + " bytes)");
@@ -973,7 +973,7 @@ extern "C" size_t ens_pcg_ir_workspace_size(int J, int64_t nnz, int S, int E)
 {
     (void)nnz;
     if (J <= 0 || E <= 0 || !lane_count_ok(S)) return 0;
-    return ir_layout(J, S, E, geometry(J, S), nullptr, nullptr);
+    return ir_layout(J, S, E, geometry(J, S, E), nullptr, nullptr);
 }
 
 extern "C" int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E, const int32_t *rowptr,
@@ -997,7 +997,7 @@ extern "C" int ens_pcg_solve_ir(ens_handle h, int J, int64_t nnz, int S, int E, 
         int crc = check_pattern(h, "ens_pcg_solve_ir", J, nnz, rowptr, colidx, (cudaStream_t)stream);
         if (crc) return crc;
     }
-    Geo g = geometry(J, S);
+    Geo g = geometry(J, S, E);
     const size_t need = ir_layout(J, S, E, g, nullptr, nullptr);
     if (work_bytes < need)
         return set_error(h, ENS_ENOMEM, "ens_pcg_solve_ir: workspace too small (need " + std::to_string(need) + " bytes)");
@@ -1194,7 +1194,7 @@ extern "C" size_t ens_stream_workspace_size(const ens_problem *p, int S, int E)
     int64_t nnz;
     std::string why;
     if (problem_check(p, &J, &nnz, &why) || !lane_count_ok(S) || E <= 0) return 0;
-    return stream_layout(J, nnz, S, E, p->nparam, geometry(J, S), nullptr, nullptr);
+    return stream_layout(J, nnz, S, E, p->nparam, geometry(J, S, E), nullptr, nullptr);
 }
 
 extern "C" int ens_solve_stream(ens_handle h, const ens_problem *p, int S, int E, int M, const double *xi,
@@ -1213,7 +1213,7 @@ extern "C" int ens_solve_stream(ens_handle h, const ens_problem *p, int S, int E
     if (E < 1 || M < 0 || chunk < 1) return set_error(h, ENS_EINVAL, "ens_solve_stream: need E >= 1, M >= 0, chunk >= 1");
     if (M == 0) return ENS_OK;
     if (!xi || !iters || !status || !relres || !work) return set_error(h, ENS_EINVAL, "ens_solve_stream: null pointer");
-    Geo g = geometry(J, S);
+    Geo g = geometry(J, S, E);
     const size_t need = stream_layout(J, nnz, S, E, p->nparam, g, nullptr, nullptr);
     if (work_bytes < need)
         return set_error(h, ENS_ENOMEM, "ens_solve_stream: workspace too small (need " + std::to_string(need) + " bytes)");
@@ -1419,7 +1419,7 @@ extern "C" int ens_pcg_solve_static(ens_handle h, int J, int64_t nnz, int S, int
         int crc = check_pattern(h, "ens_pcg_solve_static", J, nnz, rowptr, colidx, (cudaStream_t)stream);
         if (crc) return crc;
     }
-    Geo g = geometry(J, S);
+    Geo g = geometry(J, S, E);
     const size_t need = layout(J, S, E, g, nullptr, nullptr);
     if (need > kStaticScratchBytes)
         return set_error(h, ENS_EINVAL, "ens_pcg_solve_static: this problem needs " + std::to_string(need) +
@@ -1456,7 +1456,7 @@ extern "C" int ens_spmv(ens_handle h, int J, int64_t nnz, int S, int E, const in
         int crc = check_pattern(h, "ens_spmv", J, nnz, rowptr, colidx, (cudaStream_t)stream);
         if (crc) return crc;
     }
-    Geo g = geometry(J, S);
+    Geo g = geometry(J, S, E);
     const size_t need = layout(J, S, E, g, nullptr, nullptr);
     if (work_bytes < need) return set_error(h, ENS_ENOMEM, "ens_spmv: workspace too small");
     Args a;

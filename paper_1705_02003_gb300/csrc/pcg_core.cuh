@@ -61,17 +61,30 @@ struct Args {
 // problems (J <= 4096, a handful of blocks per ensemble whatever the tile) take
 // 64-row tiles instead: a thread then walks 4 rows, not 16, per kernel, which
 // shortens the latency chain of an iteration (32^2 workload: 1.29x; on 31^3,
-// where 64-row tiles make 466 blocks per ensemble, they were 10 % slower).  The
-// geometry depends on J only, so a lane's reduction order is the same for any
-// E and any lane position.
-inline Geo geometry(int J, int S)
+// where 64-row tiles make 466 blocks per ensemble, they were 10 % slower).
+//
+// For S >= 2 the geometry depends on J only, so a lane's reduction order is the
+// same for any E and any lane position.  One-lane ensembles (S = 1) are the
+// exception: with 256-row tiles a thread owns one row of a 256-row tile, which
+// leaves it no independent rows to hide the FP64 latency chain and pays a
+// block reduction per 256 row-lanes.  When the call's one-lane ensembles fill
+// the GPU (E J >= kOneLaneBatch row-lanes, three 4096-row blocks per SM) their
+// tiles are kOneLaneTile rows, 16 rows per thread as at S = 16: measured on
+// Q1 256^2 with 48-159 one-lane ensembles, 324 against 138 sample-solves/s.  A
+// single one-lane ensemble keeps the small tiles (it would run on 16 blocks:
+// 18 against 33 sample-solves/s).  So at S = 1 a sample's rounding depends on
+// whether its call holds a full batch.
+constexpr int kOneLaneTile = 4096;
+constexpr long long kOneLaneBatch = 152LL * 3 * kOneLaneTile;
+
+inline Geo geometry(int J, int S, int E)
 {
-    (void)S;
     const long long target = 152LL * 4;
     long long RT = ((long long)J + target - 1) / target;
     const long long tile = J <= 4096 ? 64 : 256;
     if (RT < tile) RT = tile;
     RT = (RT + tile - 1) / tile * tile;
+    if (S == 1 && J > 4096 && (long long)E * J >= kOneLaneBatch && RT < kOneLaneTile) RT = kOneLaneTile;
     Geo g;
     g.RT = (int)RT;
     g.nblk = (int)((J + RT - 1) / RT);

@@ -138,6 +138,23 @@ def test_pcg_full_size_sampled_lanes(h, name, lanes):
     check_against_oracle(c, got, ref, 1e-8, lanes)
 
 
+@pytest.mark.parametrize("name,M", [("q1_256_adaptive", 3), ("q1_256_adaptive", 32), ("fd7_64_batch", 3),
+                                    ("fd7_64_batch", 8)])
+def test_one_lane_ensembles_full_size(h, name, M):
+    """S = 1 on the full-size problems, M one-lane ensembles in one call: a few
+    (256-row tiles; 512 on 64^3) and a batch that fills the GPU (4096-row tiles;
+    on the 7-point 64^3 rows in dealt 256-row chunks).  Sampled lanes against
+    the oracle."""
+    wl = inputs.WORKLOADS[name]
+    xi = inputs.draws(M, wl.nparam, seed=wl.seed + 1)
+    c = Case(h, wl.kind, wl.n, wl.nparam, wl.aniso, 1, xi)
+    got = c.solve(1e-8, wl.maxit)
+    assert np.all(got["status"] == ens.LANE_CONVERGED)
+    lanes = [0, M - 1]
+    ref = oracle_solve(c, 1e-8, wl.maxit, rows=lanes)
+    check_against_oracle(c, got, ref, 1e-8, lanes)
+
+
 # ---------------------------------------------------------------------------
 # invariants (bit-exact on the GPU)
 # ---------------------------------------------------------------------------
@@ -303,7 +320,8 @@ def test_argument_errors(h):
 
 @pytest.mark.parametrize("kind,n,N,aniso,S,M", [("q1", 30, 4, 4.0, 16, 20), ("fd7", 9, 6, 3.0, 8, 9),
                                                 ("fd5", 20, 8, 3.0, 1, 3), ("fd5", 12, 2, 3.0, 64, 64),
-                                                ("fd5", 50, 4, 3.0, 16, 20), ("fd5", 40, 8, 3.0, 32, 33)])
+                                                ("fd5", 50, 4, 3.0, 16, 20), ("fd5", 40, 8, 3.0, 32, 33),
+                                                ("q1", 30, 4, 4.0, 1, 3), ("fd7", 60, 6, 3.0, 1, 2)])
 def test_spmv_matches_oracle_and_lane_dots(h, kind, n, N, aniso, S, M):
     """K2 alone: each row sum is taken in the oracle's column order, with one
     rounding per fused multiply-add instead of two, so every row agrees with

@@ -634,6 +634,12 @@ def run_c1(h, stream, hbm: float, fp64: float):
     M = len(r["I"])
     out["per_sample_serial"] = {"value": M / t, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r["I"] - ref["I"]))),
                                 **roof_fracs(M / t, M, float(r["I"].sum()), ad.solver.nnz, ad.solver.J, 1, hbm, fp64)}
+    pb = Adaptive(h, wl, S=1)  # one sample per lane, a level per call
+    pb.run("nat")
+    r, t = timed(stream, lambda: pb.run("nat"))
+    out["per_sample_batched"] = {"value": M / t, "max_iter_diff_vs_ensemble": int(np.max(np.abs(r["I"] - ref["I"]))),
+                                 **roof_fracs(M / t, M, float(r["I"].sum()), ad.solver.nnz, ad.solver.J, 1, hbm,
+                                              fp64)}
     # the same surrogate arm with every solve on the three-kernel graph loop
     # instead of the one-launch cluster schedule (identical results)
     import torch

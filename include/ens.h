@@ -183,7 +183,12 @@ size_t ens_pcg_workspace_size(int J, int64_t nnz, int S, int E);
  * graph body).  Problems of at most 1024 unknowns instead run as one kernel
  * launch (ens_pcg_cluster_size).  Results do not depend on any of these
  * choices, bit for bit: every schedule performs the same operations in the
- * same order. */
+ * same order.  A lane's results do not depend on E, on its position or on the
+ * other lanes either, with one exception: for one-lane ensembles (S = 1) on
+ * problems of more than 4096 unknowns, a call with E J >= 1,867,776 (three
+ * 4096-row blocks per SM of 152) uses 4096-row tiles instead of 256-row ones,
+ * so a sample's rounding then depends on the size of its batch (the tile
+ * sets the order of its inner-product sums). */
 int ens_pcg_solve(ens_handle h, int J, int64_t nnz, int S, int E,
                   const int32_t *rowptr, const int32_t *colidx, const double *vals,
                   const double *dinv, const double *b, double *x, const uint8_t *active,

@@ -156,3 +156,27 @@ def test_default_handle_applies_the_work_bound(ens_lib):
     J, nnz = ens.ens_problem_size(ens.problem("q1_3d_kl", 7, 4, 0.0))
     assert ens.ens_pcg_cluster_size(h, J, nnz, 8, 1) == 6
     assert ens.ens_pcg_cluster_size(h, J, nnz, 16, 1) == 0
+
+
+def test_null_active_mask(handles):
+    """active = NULL (every lane active) on both schedules."""
+    import torch
+
+    S, E = 8, 2
+    outs = []
+    for h in handles:
+        c = Case(h, "fd5", 32, 2, 3.0, S, inputs.draws(S * E, 2, seed=31))
+        J, nnz = c.J, c.nnz
+        x = torch.empty(E * J * S, dtype=torch.float64, device="cuda")
+        it = torch.empty(E * S, dtype=torch.int32, device="cuda")
+        st = torch.empty_like(it)
+        rr = torch.empty(E * S, dtype=torch.float64, device="cuda")
+        work = torch.empty(ens.ens_pcg_workspace_size(J, nnz, S, E), dtype=torch.uint8, device="cuda")
+        ens.ens_pcg_solve(h, J, nnz, S, E, c.rowptr, c.colidx, c.vals, c.dinv, c.b, x, None, 1e-8, 5000, it, rr, st,
+                          work)
+        torch.cuda.synchronize()
+        outs.append(dict(x=x.cpu().numpy(), iters=it.cpu().numpy(), status=st.cpu().numpy(),
+                         relres=rr.cpu().numpy()))
+    assert ens.ens_pcg_cluster_size(handles[0], J, nnz, S, E) > 0
+    same(outs[0], outs[1])
+    assert np.all(outs[0]["status"] == ens.LANE_CONVERGED)

@@ -168,6 +168,25 @@ __device__ __forceinline__ void combine(const double *xch, int nblk, double (&to
     }
 }
 
+// With PACK, the totals that combine left in thread ls * GS (lead) move to
+// thread ls, through shared memory; without it they stay where they are.
+// Every thread must call it.
+template <int S, int NS, bool PACK>
+__device__ __forceinline__ void to_lane_threads(double (&t)[NS], bool lead, int ls, double (*ttot)[S])
+{
+    if constexpr (PACK) {
+        if (lead) {
+#pragma unroll
+            for (int ns = 0; ns < NS; ns++) ttot[ns][ls] = t[ns];
+        }
+        __syncthreads();
+        if (threadIdx.x < S) {
+#pragma unroll
+            for (int ns = 0; ns < NS; ns++) t[ns] = ttot[ns][threadIdx.x];
+        }
+    }
+}
+
 // A row of a windowed vector (V lanes from lane0) into this CTA's window and
 // into the window of every other CTA that holds the row.  w is the window
 // array (the same offset in every CTA); CTA k's window holds rows
@@ -271,6 +290,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_cluster(Args a, int W, int vc
     const int r0 = c * kTile, r1 = min(J, r0 + kTile);
     const int tid = threadIdx.x, ls = tid / GS;
     const bool lead = tid % GS == 0 && ls < S;  // the thread that holds lane ls's totals after combine
+    // Each lane's scalar work (divides, square roots) runs in one thread.  When
+    // the combine leaves the totals in more than one warp, they first move to
+    // threads 0..S-1 of warp 0: on this part an FP64 warp instruction occupies
+    // the pipe for the whole warp, so eight warps dividing for two lanes each
+    // cost four times one warp dividing for eight.
+    constexpr bool kPack = S * GS > 32;
+    __shared__ double ttot[2][S];
+    const bool lt = kPack ? tid < S : lead;  // the thread that runs lane ln's logic
+    const int ln = kPack ? tid : ls;
     double *xa = dyn, *xb = xa + (size_t)nblk * S;
     double *ox = xb + (size_t)2 * nblk * S, *orr = ox + kTile * S, *oq = orr + kTile * S;
     double *pwin = oq + kTile * S, *zwin = pwin + (size_t)W * S;
@@ -355,8 +383,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_cluster(Args a, int W, int vc
     {
         double t[2];
         combine<S, 2>(xb, nblk, t);
-        if (lead) {
-            const int s = ls, L = e * S + s;
+        to_lane_threads<S, 2, kPack>(t, lead, ls, ttot);
+        if (lt) {
+            const int s = ln, L = e * S + s;
             const double bsq = t[0], rzs = t[1];
             const int act = a.active ? (int)a.active[L] : 1;
             int lv = 0, st;
@@ -385,7 +414,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_cluster(Args a, int W, int vc
             }
         }
     }
-    int nl = __syncthreads_count(lead && live[ls]);
+    int nl = __syncthreads_count(lt && live[ln]);
 
     int trips = 0;
     while (nl > 0 && trips < a.trip_cap) {
@@ -407,8 +436,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_cluster(Args a, int W, int vc
         {
             double t[1];
             combine<S, 1>(xa, nblk, t);
-            if (lead && live[ls]) {
-                const int s = ls, L = e * S + s;
+            to_lane_threads<S, 1, kPack>(t, lead, ls, ttot);
+            if (lt && live[ln]) {
+                const int s = ln, L = e * S + s;
                 const double pq = t[0];
                 if (!(pq > 0.0) || !isfinite(pq)) {
                     // zero (or invalid) A-conjugate norm: freeze, x stays as it is
@@ -475,8 +505,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_cluster(Args a, int W, int vc
         {
             double t[2];
             combine<S, 2>(xb, nblk, t);
-            if (lead && live[ls]) {
-                const int s = ls, L = e * S + s;
+            to_lane_threads<S, 2, kPack>(t, lead, ls, ttot);
+            if (lt && live[ln]) {
+                const int s = ln, L = e * S + s;
                 const int k = kk[s] + 1;
                 kk[s] = k;
                 const double rsq = t[0], rzn = t[1];
@@ -496,7 +527,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_cluster(Args a, int W, int vc
                 }
             }
         }
-        nl = __syncthreads_count(lead && live[ls]);
+        nl = __syncthreads_count(lt && live[ln]);
         trips++;
         if (nl == 0 || trips >= a.trip_cap) break;
 
@@ -541,11 +572,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_cluster(Args a, int W, int vc
     }
 
     // lanes still live when the trip cap stopped the loop
-    if (out && lead && live[ls]) {
-        const int L = e * S + ls;
+    if (out && lt && live[ln]) {
+        const int L = e * S + ln;
         a.status[L] = ENS_LANE_MAXIT;
-        a.iters[L] = kk[ls];
-        a.relres[L] = sqrt(rr[ls]) / bnorm[ls];
+        a.iters[L] = kk[ln];
+        a.relres[L] = sqrt(rr[ln]) / bnorm[ln];
     }
     {
         constexpr int V = VG::V, TPR = VG::TPR, RPP = VG::RPP;

@@ -747,6 +747,18 @@ def run_paper(h, stream, S_list=(4, 8, 16, 32)):
                    "iters_min": int(r0["I"].min()), "iters_max": int(r0["I"].max()),
                    "iters_mean": float(r0["I"].mean()), "sequential_solve_ms": t_seq,
                    "sigma_sample_iters": int(r0["I"][j_med]), "sigma_one_solve_ms": t1, "S": {}}
+            # one sample per lane, a level per call (S = 1): independent per-sample
+            # solves batched, against which the ensembles' speed-up is also quoted
+            one = Adaptive(h, wl, S=1, precond=pc)
+            one.run("nat")  # warm-up
+            one.time_calls = True
+            r1 = one.run("nat")
+            t_one = solve_ms(one)
+            res["one_lane_batch"] = {"solve_ms": t_one, "speedup": t_seq / t_one,
+                                     "same_grid": bool(np.array_equal(r1["lvl"], r0["lvl"])),
+                                     "max_iter_diff_vs_sequential": int(np.max(np.abs(r1["I"] - r0["I"])))}
+            del one
+            torch.cuda.empty_cache()
             for S in S_list:
                 ad = Adaptive(h, wl, S=S, precond=pc)
                 ad.run("nat")  # warm-up: instantiates every level's loop graph
@@ -765,7 +777,8 @@ def run_paper(h, stream, S_list=(4, 8, 16, 32)):
                     same_grid &= bool(np.array_equal(r["lvl"], r0["lvl"]))
                     R = ratios(r)
                     row[g] = {"R_levels": R["run"][0], "R": R["run"][1], "speedup": t_seq / t,
-                              "pred_speedup": sigma / R["run"][1], "solve_ms": t}
+                              "pred_speedup": sigma / R["run"][1], "solve_ms": t,
+                              "vs_one_lane_batch": t_one / t}
                     if g == "sur":
                         row["its"] = {"R_levels": R["its"][0], "R": R["its"][1],
                                       "pred_speedup": sigma / R["its"][1]}

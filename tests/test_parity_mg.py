@@ -127,13 +127,14 @@ def _check(got, ref, lanes, bar):
         assert err <= (bar if di == 0 else 1e-5), (L, err)
 
 
+@pytest.mark.parametrize("S", [16, 1])
 @pytest.mark.parametrize("kind", KINDS)
-def test_mgpcg_matches_oracle_on_the_oracles_matrices(h, kind):
+def test_mgpcg_matches_oracle_on_the_oracles_matrices(h, kind, S):
     """The solver alone (both sides from the oracle's matrices and loads):
     iterations within 1, x within 1e-9 when the counts agree.  The
     preconditioned operator is well conditioned, so rounding moves the iterate
-    far less than in the Jacobi solve."""
-    n, S, M = 15, 16, 21
+    far less than in the Jacobi solve.  S = 1: 21 one-lane ensembles."""
+    n, M = 15, 21
     c = Case(h, kind, n, 4, 0.0, S, draws(M, 13))
     rp, ci, V, B, vals, b = oracle_system(c, kind)
     got = c.solve_mg(1e-7, 500, vals=vals, b=b)
@@ -142,12 +143,13 @@ def test_mgpcg_matches_oracle_on_the_oracles_matrices(h, kind):
     assert all(got["status"][M:] == ens.LANE_INACTIVE)
 
 
+@pytest.mark.parametrize("S", [16, 1])
 @pytest.mark.parametrize("kind", KINDS)
-def test_mixed_mgpcg_matches_oracle_on_the_oracles_matrices(h, kind):
+def test_mixed_mgpcg_matches_oracle_on_the_oracles_matrices(h, kind, S):
     """CG in FP64 with the float V-cycle, on the oracle's matrices and loads:
     iterations within 1 of the oracle's CG with its float V-cycle, x within 1e-6
     when the counts agree (the two float preconditioners differ at ~1e-7)."""
-    n, S, M = 15, 16, 21
+    n, M = 15, 21
     c = Case(h, kind, n, 4, 0.0, S, draws(M, 17))
     rp, ci, V, B, vals, b = oracle_system(c, kind)
     got = c.solve_mg(1e-7, 500, vals=vals, b=b, mixed=True)

@@ -16,7 +16,10 @@ around K steps, max over ranks).
 The LAST line on stdout is one compact JSON object: metric, value, config,
 roofline of the dominant kernel (K2, against the FP64 issue rate measured in
 the same run, with the HBM view beside it), cpu_baseline, e2e, clocks and the
-speed-up over one-sample-at-a-time PCG.  Everything else goes to the detail
+speed-up over per-sample PCG, both one sample at a time and as a batch of
+one-lane ensembles (on this problem the batch is the faster of the two, and
+faster than the ensemble: the path is bound by FP64 issue, not by memory).
+Everything else goes to the detail
 file (--detail-out, default <tmpdir>/ens_bench_detail.json):
   arms            parameter-based, natural and random grouping; one sample per
                   call (serial) and all samples of a level in one call at S = 1

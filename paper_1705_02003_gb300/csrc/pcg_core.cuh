@@ -63,9 +63,17 @@ struct Args {
 // shortens the latency chain of an iteration (32^2 workload: 1.29x; on 31^3,
 // where 64-row tiles make 466 blocks per ensemble, they were 10 % slower).
 //
-// For S >= 2 the geometry depends on J only, so a lane's reduction order is the
-// same for any E and any lane position.  One-lane ensembles (S = 1) are the
-// exception: with 256-row tiles a thread owns one row of a 256-row tile, which
+// Small ensembles (S = 2, 4, 8; J > 4096) take tiles of 256 x 16 / S rows, so
+// that a K2 thread walks 16 rows per tile as it does at S = 16 (with 256-row
+// tiles an S = 4 thread had 4 rows: little independent work to hide the FP64
+// latency chain).  Measured on the Q1 256^2 loop with surrogate grouping:
+// S = 4 230 -> 299 sample-solves/s, S = 8 279 -> 294; on Section 4's Test 1
+// S = 4 +10 %, S = 8 unchanged.  A single small ensemble then runs on fewer
+// blocks (64 at S = 4 on 65536 unknowns).
+//
+// For S >= 2 the geometry depends on J and S only, so a lane's reduction order
+// is the same for any E and any lane position.  One-lane ensembles (S = 1) are
+// the exception: with 256-row tiles a thread owns one row of a 256-row tile, which
 // leaves it no independent rows to hide the FP64 latency chain and pays a
 // block reduction per 256 row-lanes.  When the call's one-lane ensembles fill
 // the GPU (E J >= kOneLaneBatch row-lanes, three 4096-row blocks per SM) their
@@ -84,6 +92,7 @@ inline Geo geometry(int J, int S, int E)
     const long long tile = J <= 4096 ? 64 : 256;
     if (RT < tile) RT = tile;
     RT = (RT + tile - 1) / tile * tile;
+    if (S >= 2 && S <= 8 && J > 4096 && RT < 4096LL / S) RT = 4096LL / S;
     if (S == 1 && J > 4096 && (long long)E * J >= kOneLaneBatch && RT < kOneLaneTile) RT = kOneLaneTile;
     Geo g;
     g.RT = (int)RT;

@@ -155,6 +155,23 @@ def test_one_lane_ensembles_full_size(h, name, M):
     check_against_oracle(c, got, ref, 1e-8, lanes)
 
 
+@pytest.mark.parametrize("S", [2, 4, 8])
+def test_small_ensembles_full_size(h, S):
+    """S = 2, 4, 8 on Q1 256^2 (tiles of 4096 / S rows, whatever E): a sample
+    gives the same bits alone and in a batch of three ensembles, and sampled
+    lanes agree with the oracle."""
+    wl = inputs.WORKLOADS["q1_256_adaptive"]
+    xi = inputs.draws(3 * S, wl.nparam, seed=wl.seed + 2)
+    c = Case(h, wl.kind, wl.n, wl.nparam, wl.aniso, S, xi)
+    batch = c.solve(1e-8, wl.maxit)
+    alone = Case(h, wl.kind, wl.n, wl.nparam, wl.aniso, S, xi[S:2 * S]).solve(1e-8, wl.maxit)
+    assert np.array_equal(batch["x"][S:2 * S], alone["x"])
+    assert np.array_equal(batch["iters"][S:2 * S], alone["iters"])
+    assert np.all(batch["status"] == ens.LANE_CONVERGED)
+    lanes = [0, 2 * S - 1]
+    check_against_oracle(c, batch, oracle_solve(c, 1e-8, wl.maxit, rows=lanes), 1e-8, lanes)
+
+
 # ---------------------------------------------------------------------------
 # invariants (bit-exact on the GPU)
 # ---------------------------------------------------------------------------
